@@ -1,0 +1,190 @@
+"""ctypes wrapper of the FP64 CPU oracle (test infrastructure only).
+
+The C source is compiled on first use by ``oracle.build``. Arrays are numpy
+float64 in the library layout: scalar fields ``[z][y][x]`` flattened, vector
+fields as D planes, populations as Q planes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+ZETA_LITERAL = 1
+PHI_OFF = 2
+FORCE_PRINTED_SIGN = 4
+PHI_PRINTED_SIGN = 8
+
+EOS_VDW, EOS_PR, EOS_RKS, EOS_CS = 0, 1, 2, 3
+
+# Default EOS constants (lattice units): van der Waals a = 9/49, b = 2/21;
+# Peng-Robinson and Redlich-Kwong-Soave a = 2/49, b = 2/21, acentric 0.344
+# (the paper's water value, Sec. 3.1); Carnahan-Starling a = 1, b = 4.
+DEFAULT_AB = {EOS_VDW: (9.0 / 49.0, 2.0 / 21.0), EOS_PR: (2.0 / 49.0, 2.0 / 21.0),
+              EOS_RKS: (2.0 / 49.0, 2.0 / 21.0), EOS_CS: (1.0, 4.0)}
+DEFAULT_ACENTRIC = 0.344
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(_build.build())
+        L.oracle_create.restype = C.c_void_p
+        L.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                    C.c_double, C.c_double, C.c_void_p, C.c_double,
+                                    C.c_double, C.c_double, C.c_double, C.c_int]
+        L.oracle_destroy.argtypes = [C.c_void_p]
+        L.oracle_init.argtypes = [C.c_void_p, _dp, _dp]
+        L.oracle_step.argtypes = [C.c_void_p, C.c_long]
+        L.oracle_moments.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+        L.oracle_reduce.argtypes = [C.c_void_p, _dp, _dp]
+        L.oracle_get_populations.argtypes = [C.c_void_p, _dp]
+        L.oracle_set_populations.argtypes = [C.c_void_p, _dp]
+        L.oracle_feq.argtypes = [C.c_void_p, C.c_double, _dp, _dp]
+        L.oracle_fstar.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp, _dp]
+        L.oracle_stencil.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
+        L.oracle_weights.argtypes = [C.c_void_p, _dp, C.POINTER(C.c_int)]
+        L.oracle_rt.restype = C.c_double
+        L.oracle_rt.argtypes = [C.c_void_p]
+        L.oracle_alpha.restype = C.c_double
+        L.oracle_alpha.argtypes = [C.c_void_p]
+        L.oracle_eos_pressure.restype = C.c_double
+        L.oracle_eos_pressure.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, C.c_double]
+        L.oracle_eos_RTc.restype = C.c_double
+        L.oracle_eos_RTc.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.oracle_eos_alpha.restype = C.c_double
+        L.oracle_eos_alpha.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.oracle_eos_pressure_array.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                                C.c_double, _dp, C.c_long, _dp]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+class EOS:
+    """P(rho) at fixed T/Tc through the oracle's C equation of state."""
+
+    def __init__(self, eos: int, t_over_tc: float, a: float | None = None,
+                 b: float | None = None, acentric: float = DEFAULT_ACENTRIC):
+        da, db = DEFAULT_AB[eos]
+        self.eos = eos
+        self.a = da if a is None else a
+        self.b = db if b is None else b
+        self.acentric = acentric
+        self.t_over_tc = t_over_tc
+        L = lib()
+        self.RTc = L.oracle_eos_RTc(eos, self.a, self.b)
+        self.RT = t_over_tc * self.RTc
+        self.alpha = L.oracle_eos_alpha(eos, acentric, t_over_tc)
+
+    def __call__(self, rho):
+        r = np.ascontiguousarray(np.atleast_1d(np.asarray(rho, dtype=np.float64)))
+        out = np.empty_like(r)
+        lib().oracle_eos_pressure_array(self.eos, self.a, self.b, self.RT, self.alpha,
+                                        _p(r), r.size, _p(out))
+        return out if np.ndim(rho) else float(out[0])
+
+
+class OracleLBM:
+    """One lattice on the CPU oracle."""
+
+    def __init__(self, lattice: int, nx: int, ny: int, nz: int, eos: int, t_over_tc: float,
+                 kappa: float, tau: float, mask: np.ndarray | None = None,
+                 a: float | None = None, b: float | None = None,
+                 acentric: float = DEFAULT_ACENTRIC, rho_w: float = 1.0, flags: int = 0):
+        self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
+        self.D = 2 if lattice == 0 else 3
+        self.Q = 9 if lattice == 0 else 27
+        self.N = nx * ny * nz
+        da, db = DEFAULT_AB[eos]
+        a = da if a is None else a
+        b = db if b is None else b
+        self._mask = None
+        mp = None
+        if mask is not None:
+            self._mask = np.ascontiguousarray(mask, dtype=np.uint8)
+            assert self._mask.size == self.N
+            mp = self._mask.ctypes.data_as(C.c_void_p)
+        self._h = lib().oracle_create(lattice, nx, ny, nz, eos, t_over_tc, kappa, tau, mp,
+                                      a, b, acentric, rho_w, flags)
+        if not self._h:
+            raise ValueError("oracle_create rejected the arguments")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().oracle_destroy(h)
+            self._h = None
+
+    def init(self, rho0: np.ndarray, u0: np.ndarray | None = None):
+        r = np.ascontiguousarray(rho0, dtype=np.float64)
+        u = np.ascontiguousarray(u0 if u0 is not None else np.zeros(self.D * self.N),
+                                 dtype=np.float64)
+        lib().oracle_init(self._h, _p(r), _p(u))
+
+    def step(self, n: int = 1):
+        lib().oracle_step(self._h, n)
+
+    def moments(self):
+        rho = np.empty(self.N)
+        u = np.empty(self.D * self.N)
+        U = np.empty(self.D * self.N)
+        F = np.empty(self.D * self.N)
+        lib().oracle_moments(self._h, _p(rho), _p(u), _p(U), _p(F))
+        return rho, u, U, F
+
+    def reduce(self):
+        m = C.c_double()
+        j = np.zeros(3)
+        lib().oracle_reduce(self._h, C.byref(m), _p(j))
+        return m.value, j[: self.D].copy()
+
+    def get_populations(self) -> np.ndarray:
+        out = np.empty(self.Q * self.N)
+        lib().oracle_get_populations(self._h, _p(out))
+        return out
+
+    def set_populations(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.Q * self.N
+        lib().oracle_set_populations(self._h, _p(f))
+
+    def feq(self, rho: float, u) -> np.ndarray:
+        uu = np.zeros(3)
+        uu[: self.D] = u
+        out = np.empty(self.Q)
+        lib().oracle_feq(self._h, rho, _p(uu), _p(out))
+        return out
+
+    def fstar(self, rho: float, u, F, Phi) -> np.ndarray:
+        uu, FF, PP = np.zeros(3), np.zeros(3), np.zeros(3)
+        uu[: self.D], FF[: self.D], PP[: self.D] = u, F, Phi
+        out = np.empty(self.Q)
+        lib().oracle_fstar(self._h, rho, _p(uu), _p(FF), _p(PP), _p(out))
+        return out
+
+    def stencil(self, g: np.ndarray, g1: float, g2: float) -> np.ndarray:
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        out = np.zeros(3 * self.N)
+        lib().oracle_stencil(self._h, _p(g), g1, g2, _p(out))
+        return out[: self.D * self.N].copy()
+
+    def weights(self):
+        w = np.empty(self.Q)
+        c = np.empty(3 * self.Q, dtype=np.int32)
+        lib().oracle_weights(self._h, _p(w), c.ctypes.data_as(C.POINTER(C.c_int)))
+        return w, c.reshape(self.Q, 3)
+
+    @property
+    def RT(self) -> float:
+        return lib().oracle_rt(self._h)

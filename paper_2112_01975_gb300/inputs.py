@@ -1,0 +1,174 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the bench.
+
+This module holds no arithmetic of the lattice Boltzmann method itself: it
+only draws seeded numbers and lays out initial density/velocity fields and
+solid masks on the lattice. Every field is returned as float64 numpy arrays in
+the library's layout: scalar fields ``[z][y][x]`` flattened with x fastest,
+vector fields as ``D`` consecutive planes of that shape.
+
+Noise: ``xi = U[-1, 1)`` from splitmix64(seed XOR linear index), the published
+counter-based generator of Steele, Lea and Flood (2014), written out here.
+
+Initial drop profile: a tanh between the two coexistence densities whose
+maximum slope equals the interface-width definition W = (rho_l - rho_v) /
+max|grad rho| of Sec. 3.5 (Eq. interface_W).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser applied to each uint64 of ``x``."""
+    with np.errstate(over="ignore"):
+        z = (x.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_pm1(seed: int, n: int) -> np.ndarray:
+    """n draws of U[-1, 1): top 53 bits of splitmix64(seed ^ i), i = 0..n-1."""
+    idx = np.arange(n, dtype=np.uint64) ^ np.uint64(seed & _M64)
+    bits = splitmix64(idx) >> np.uint64(11)
+    return bits.astype(np.float64) * (2.0 ** -53) * 2.0 - 1.0
+
+
+def _coords(nx: int, ny: int, nz: int):
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64),
+                          np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def tanh_interface(dist: np.ndarray, rho_in: float, rho_out: float,
+                   width: float) -> np.ndarray:
+    """rho_in where dist << 0, rho_out where dist >> 0, max slope
+    (rho_in - rho_out) / width at dist = 0."""
+    return 0.5 * (rho_in + rho_out) - 0.5 * (rho_in - rho_out) * np.tanh(2.0 * dist / width)
+
+
+def drop(nx: int, ny: int, nz: int, radius: float, rho_v: float, rho_l: float,
+         width: float = 5.0, center=None) -> np.ndarray:
+    """Liquid drop of the given radius centred at (nx/2, ny/2[, nz/2])."""
+    x, y, z = _coords(nx, ny, nz)
+    cx, cy, cz = center if center is not None else (nx // 2, ny // 2, nz // 2 if nz > 1 else 0)
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + ((z - cz) ** 2 if nz > 1 else 0.0))
+    return tanh_interface(r - radius, rho_l, rho_v, width).ravel()
+
+
+def drops(nx: int, ny: int, nz: int, centers, radius: float, rho_v: float,
+          rho_l: float, width: float = 5.0) -> np.ndarray:
+    """Several drops: pointwise maximum of single-drop profiles."""
+    out = None
+    for c in centers:
+        d = drop(nx, ny, nz, radius, rho_v, rho_l, width, center=c)
+        out = d if out is None else np.maximum(out, d)
+    return out
+
+
+def slab(nx: int, ny: int, nz: int, x0: float, x1: float, rho_v: float,
+         rho_l: float, width: float = 5.0) -> np.ndarray:
+    """Liquid for x0 <= x < x1 (flat interfaces normal to x), vapour elsewhere."""
+    x, _, _ = _coords(nx, ny, nz)
+    mid = 0.5 * (x0 + x1)
+    half = 0.5 * (x1 - x0)
+    return tanh_interface(np.abs(x - mid) - half, rho_l, rho_v, width).ravel()
+
+
+def add_noise(rho: np.ndarray, rel: float, seed: int) -> np.ndarray:
+    """rho * (1 + rel * xi), xi = U[-1, 1) from splitmix64(seed ^ index)."""
+    return rho * (1.0 + rel * uniform_pm1(seed, rho.size))
+
+
+def pillar_mask(nx: int, ny: int, nz: int, side: int = 8, height: int = 16,
+                pitch: int = 16, seed: int = 4) -> np.ndarray:
+    """uint8 solid mask: wall at z = 0 plus square pillars (side x side x
+    height) on a square lattice of the given pitch, on z = 1..height. The
+    pillar lattice offset in x and y comes from the seed."""
+    off = splitmix64(np.array([seed], dtype=np.uint64))[0]
+    ox = int(off % np.uint64(pitch))
+    oy = int((off >> np.uint64(32)) % np.uint64(pitch))
+    m = np.zeros((nz, ny, nx), dtype=np.uint8)
+    m[0] = 1
+    xs = ((np.arange(nx) - ox) % pitch) < side
+    ys = ((np.arange(ny) - oy) % pitch) < side
+    col = np.logical_and(ys[:, None], xs[None, :])
+    m[1:1 + height][:, col] = 1
+    return m.ravel()
+
+
+def block_mask(nx: int, ny: int, nz: int, lo, hi) -> np.ndarray:
+    """uint8 mask with one solid box lo <= (x, y, z) < hi."""
+    m = np.zeros((nz, ny, nx), dtype=np.uint8)
+    m[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = 1
+    return m.ravel()
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One synthetic workload: lattice, sizes, fluid parameters, init recipe.
+
+    ``rho_v``/``rho_l`` are the Maxwell equal-area coexistence densities of
+    the EOS at ``t_over_tc`` (eq. Maxwell_equal_area) and ``kappa`` the
+    capillary coefficient that gives a second-gradient interface width of 5
+    lattice units; both are recomputed from the EOS by a CPU test.
+    """
+    name: str
+    lattice: int          # 0 = D2Q9, 1 = D3Q27
+    nx: int
+    ny: int
+    nz: int
+    eos: int              # 0 vdW, 1 PR, 2 RKS, 3 CS
+    t_over_tc: float
+    kappa: float
+    tau: float
+    rho_v: float
+    rho_l: float
+    radius: float
+    seed: int
+    a: float
+    b: float
+    noise: float = 1e-4
+    steps: int = 1000
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def rho0(self) -> np.ndarray:
+        r = drop(self.nx, self.ny, self.nz, self.radius, self.rho_v, self.rho_l)
+        return add_noise(r, self.noise, self.seed)
+
+    def u0(self) -> np.ndarray:
+        d = 2 if self.lattice == 0 else 3
+        return np.zeros(d * self.nodes)
+
+
+# The EOS attraction parameter a is the named one scaled down by corresponding
+# states (coexistence densities depend on T/Tc and b only): with a = 9/49 the
+# liquid's isothermal sound speed squared dP/drho is 1.13 in lattice units and
+# the explicit update diverges within ten steps; a/10 gives 0.113. kappa is
+# scaled with a so that the interface width stays 5.
+
+# D2Q9 static drop, 64x64 periodic, van der Waals (a = 9/490, b = 2/21) at
+# T/Tc = 0.8, drop radius 16, tau = 1.
+DROP_D2Q9_64 = Workload("d2q9_drop_64x64_vdw_tr0.8", 0, 64, 64, 1, 0, 0.8,
+                        kappa=0.0255116006, tau=1.0, rho_v=0.838834226444,
+                        rho_l=6.76447040010, radius=16.0, seed=1,
+                        a=9.0 / 490.0, b=2.0 / 21.0, steps=1000)
+
+# D3Q27 static drop, 128^3 periodic, Peng-Robinson (a = 2/245, b = 2/21,
+# acentric factor 0.344) at T/Tc = 0.7, drop radius 24, tau = 1.
+DROP_D3Q27_128 = Workload("d3q27_drop_128^3_pr_tr0.7", 1, 128, 128, 128, 1, 0.7,
+                          kappa=0.0223020350, tau=1.0, rho_v=0.0556350874516,
+                          rho_l=8.08032155174, radius=24.0, seed=2,
+                          a=2.0 / 245.0, b=2.0 / 21.0, steps=20000)
+
+WORKLOADS = {w.name: w for w in (DROP_D2Q9_64, DROP_D3Q27_128)}

@@ -1,0 +1,125 @@
+"""Physics pins of the oracle against closed forms the paper states.
+
+- Coexistence densities of a flat interface against the Maxwell rule
+  (Sec. 3.1); the printed force sign gives no coexistence.
+- Shear-wave decay at the viscosity mu = (1/omega - 1/2) P0 (Sec. 2.3.5).
+- The same decay between two halfway bounce-back walls: the wall sits half a
+  link beyond the last fluid node.
+- Normal-mode decay independent of the frame velocity with the correction
+  Phi, frame-dependent without it or with the printed sign (Sec. 4.2).
+"""
+import numpy as np
+import pytest
+
+from oracle import physics as ph
+from oracle.lbm import EOS, FORCE_PRINTED_SIGN, OracleLBM, PHI_OFF, PHI_PRINTED_SIGN
+from paper_2112_01975_gb300.inputs import slab
+
+A_VDW = 9 / 490
+
+
+def _slab_run(flags, steps=4500):
+    e = EOS(0, 0.8, a=A_VDW)
+    rv, rl, ps = ph.maxwell(e)
+    kap = ph.kappa_for_width(e, 5.0, (rv, rl, ps))
+    nx = 128
+    o = OracleLBM(0, nx, 5, 1, 0, 0.8, kap, 1.0, a=A_VDW, flags=flags)
+    o.init(slab(nx, 5, 1, 32, 96, rv, rl, 5.0))
+    o.step(steps)
+    r = o.moments()[0].reshape(5, nx)[2]
+    return r, rv, rl
+
+
+def test_flat_interface_coexistence_matches_maxwell():
+    r, rv, rl = _slab_run(0)
+    assert abs(r[0] / rv - 1) < 0.01          # vapour, far from both interfaces
+    assert abs(r[64] / rl - 1) < 0.01         # liquid centre
+    width = (r.max() - r.min()) / np.abs(np.gradient(r)).max()
+    assert 5.0 < width < 6.5                  # second-gradient width 5, lattice-resolved
+
+
+def test_printed_force_sign_gives_no_coexistence():
+    with np.errstate(all="ignore"):
+        r, rv, rl = _slab_run(FORCE_PRINTED_SIGN, steps=600)
+    assert not (np.isfinite(r).all() and abs(r[0] / rv - 1) < 0.1 and abs(r[64] / rl - 1) < 0.1)
+
+
+def _shear_rate(lattice, tau, nx=32):
+    nz = 1 if lattice == 0 else 5
+    D = 2 if lattice == 0 else 3
+    o = OracleLBM(lattice, nx, 5, nz, 0, 0.8, 0.02, tau, a=A_VDW)
+    k = 2 * np.pi / nx
+    u = np.zeros((D, nz, 5, nx))
+    u[1] = 1e-3 * np.sin(k * np.arange(nx))
+    o.init(np.full(o.N, 2.0), u.ravel())
+    ts, amps = [], []
+    for s in range(0, 401, 50):
+        if s:
+            o.step(50)
+        uy = o.moments()[1].reshape(D, nz, 5, nx)[1, 0, 0]
+        amps.append(2 * np.abs(np.fft.rfft(uy)[1]) / nx)
+        ts.append(s)
+    return -np.polyfit(ts, np.log(amps), 1)[0], k
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+@pytest.mark.parametrize("tau", [0.8, 1.0])
+def test_shear_wave_viscosity(lattice, tau):
+    """u_y(x) decays as exp(-nu k^2 t), nu = mu/rho = (tau - 1/2)/3."""
+    rate, k = _shear_rate(lattice, tau)
+    nu = (tau - 0.5) / 3
+    assert rate == pytest.approx(nu * k * k, rel=5e-3)
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.0])
+def test_halfway_bounce_back_wall_position(tau):
+    """Between solid rows y = 0 and y = H + 1 the slowest shear mode is
+    sin(pi (y - 1/2) / H): walls at y = 1/2 and y = H + 1/2."""
+    H = 16
+    ny, nx = H + 2, 5
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = mask[-1] = 1
+    o = OracleLBM(0, nx, ny, 1, 0, 0.8, 0.02, tau, a=A_VDW, mask=mask.ravel(), rho_w=2.0)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    ux = 1e-3 * np.sin(np.pi * (y - 0.5) / H)
+    ux[0] = ux[-1] = 0
+    o.init(np.full(o.N, 2.0), np.stack([ux, np.zeros_like(ux)]).ravel())
+    mode = np.sin(np.pi * (np.arange(1, ny - 1) - 0.5) / H)
+    ts, amps = [], []
+    for s in range(0, 801, 100):
+        if s:
+            o.step(100)
+        amps.append(o.moments()[1].reshape(2, ny, nx)[0][1:-1, 0] @ mode)
+        ts.append(s)
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    assert rate == pytest.approx((tau - 0.5) / 3 * (np.pi / H) ** 2, rel=5e-3)
+
+
+def _acoustic_rate(U0, flags):
+    e = EOS(0, 0.8, a=A_VDW)
+    _, rl, _ = ph.maxwell(e)
+    nx = 64
+    o = OracleLBM(0, nx, 5, 1, 0, 0.8, 0.02, 0.6, a=A_VDW, flags=flags)
+    k = 2 * np.pi / nx
+    rho = (rl * (1 + 1e-4 * np.sin(k * np.arange(nx))))[None, :] * np.ones((5, 1))
+    u = np.zeros((2, 5, nx))
+    u[0] = U0
+    o.init(rho.ravel(), u.ravel())
+    cs2 = (e(rl * (1 + 1e-6)) - e(rl * (1 - 1e-6))) / (2e-6 * rl)
+    ts, en = [], []
+    for s in range(0, 1201, 20):
+        if s:
+            o.step(20)
+        r, _, U, _ = o.moments()
+        dr = np.fft.rfft(r.reshape(5, nx)[2])[1]
+        du = np.fft.rfft(U.reshape(2, 5, nx)[0][2])[1]
+        en.append(cs2 * abs(dr) ** 2 / rl + rl * abs(du) ** 2)
+        ts.append(s)
+    return -np.polyfit(ts[5:], np.log(en[5:]), 1)[0] / 2
+
+
+def test_correction_restores_galilean_invariance():
+    g0 = _acoustic_rate(0.0, 0)
+    assert _acoustic_rate(0.2, 0) == pytest.approx(g0, rel=3e-3)
+    assert abs(_acoustic_rate(0.2, PHI_OFF) / g0 - 1) > 0.1
+    assert abs(_acoustic_rate(0.2, PHI_PRINTED_SIGN) / g0 - 1) > 0.2
