@@ -1,0 +1,278 @@
+"""Throughput of the two-phase lattice Boltzmann step on GB300.
+
+Workload: D3Q27 static drop, 128^3 periodic, Peng-Robinson EOS at T/Tc = 0.7,
+drop radius 24, FP64 (seeded synthetic init, see paper_2112_01975_gb300/inputs.py).
+One bench step = one lattice time step over all 128^3 nodes (moments, EOS,
+Korteweg force, correction, collision, streaming). Metric: MLUPS (million
+lattice-node updates per second), whole job. The population buffers
+(2 x 453 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun), every rank advances its own replica (the method has no
+cross-lattice exchange in this workload): weak scaling, max time over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALG_BYTES_PER_LU = {  # populations read once and written once per lattice update
+    (1, 0): 2 * 27 * 8,
+    (0, 0): 2 * 9 * 8,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="d3q27_drop_128^3_pr_tr0.7")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def oracle_sample_mlups(w, target_s: float = 12.0):
+    """Single-thread FP64 oracle throughput on a centred crop of the workload."""
+    from oracle.lbm import OracleLBM
+    from paper_2112_01975_gb300 import inputs
+    n = 48 if w.lattice == 1 else 64
+    nz = n if w.lattice == 1 else 1
+    rho = inputs.add_noise(inputs.drop(n, n, nz, w.radius * n / w.nx, w.rho_v, w.rho_l),
+                           w.noise, w.seed)
+    o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b)
+    o.init(rho)
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < target_s:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return n * n * nz * steps / dt / 1e6, f"{n}x{n}x{nz} centred crop of the workload, {steps} steps, {dt:.1f} s"
+
+
+def run_reference(args, w, world, rank):
+    """The CPU oracle as it stands, one host thread, each step one lattice
+    update of a 32^3 (3D) or 64^2 (2D) crop of the workload."""
+    if rank != 0:
+        return
+    from oracle.lbm import OracleLBM
+    from paper_2112_01975_gb300 import inputs
+    n = 32 if w.lattice == 1 else 64
+    nz = n if w.lattice == 1 else 1
+    rho = inputs.add_noise(inputs.drop(n, n, nz, w.radius * n / w.nx, w.rho_v, w.rho_l),
+                           w.noise, w.seed)
+    o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b)
+    o.init(rho)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    mlups = n * n * nz * args.steps / dt / 1e6
+    sample = f"{n}x{n}x{nz} centred crop of {w.name}, one lattice update per step"
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "lattice": "D3Q27" if w.lattice else "D2Q9",
+                   "nodes": w.nodes, "storage": "f64"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    from paper_2112_01975_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, w, world, rank)
+        return
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import numpy as np
+    import torch
+    from paper_2112_01975_gb300.lbm import LBM
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    stream = torch.cuda.Stream()
+    g = LBM(w.lattice, w.nx, w.ny, w.nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
+            stream=stream)
+    rho0 = w.rho0()
+    g.init(rho0)
+    g.step(args.warmup)
+    g.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        l0 = g.launches
+        e0.record(stream)
+        g.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        l1 = g.launches
+        barrier()
+    g.sync()
+    ms = e0.elapsed_time(e1)
+    tmax = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    mlups = w.nodes * args.steps * world / (tmax * 1e-3) / 1e6
+
+    # per-kernel durations (plain launches with events between kernels)
+    n_t = max(5, min(50, args.steps // 4))
+    ms_macro, ms_collide = g.time_kernels(n_t)
+    peak, peak_kind = measured_peaks()
+    alg = ALG_BYTES_PER_LU[(w.lattice, 0)] * w.nodes
+    achieved = alg / (ms_collide * 1e-3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    pin_rho0 = torch.from_numpy(rho0).pin_memory()
+    out_rho = torch.empty(w.nodes, dtype=torch.float64).pin_memory()
+    out_u = torch.empty(3 * w.nodes if w.lattice else 2 * w.nodes, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    g.init(pin_rho0.numpy())
+    g.step(args.steps)
+    from paper_2112_01975_gb300.lbm import _lib
+    import ctypes
+    g._check(_lib.lbm_moments(g._h, ctypes.c_void_p(out_rho.data_ptr()),
+                              ctypes.c_void_p(out_u.data_ptr()), None, 0))
+    t_e2e = time.perf_counter() - t0
+    barrier()
+    e2e_mlups = w.nodes * args.steps * world / t_e2e / 1e6
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mlups = w.nodes * args.steps * world / float(t.item()) / 1e6
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, sample = oracle_sample_mlups(w)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "lattice": "D3Q27" if w.lattice else "D2Q9",
+                   "nodes": w.nodes, "storage": "f64", "eos": "Peng-Robinson" if w.eos == 1 else "vdW",
+                   "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (27 * 8 * w.nodes / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_collide",
+                     "peak_source": peak_kind, "alg_bytes_per_launch": alg,
+                     "ms_per_launch": ms_collide, "ms_moments_kernel": ms_macro},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS",
+                "h2d_bytes_per_step": 8 * w.nodes / args.steps,
+                "d2h_bytes_per_step": 8 * (1 + (3 if w.lattice else 2)) * w.nodes / args.steps},
+        "gpu_launches": l1 - l0,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

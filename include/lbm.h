@@ -1,0 +1,169 @@
+/*
+ * lbm.h - C ABI of the GB300 two-phase lattice Boltzmann library (liblbm.so).
+ *
+ * The library advances the kinetic model of Hosseini, Dorschner & Karlin,
+ * "Towards a consistent lattice Boltzmann model for two-phase fluids"
+ * (arXiv 2112.01975), on the D2Q9 and D3Q27 lattices, one GPU per handle.
+ * One time step (Sec. 2.3) is:
+ *   moments            rho = sum_i f_i, rho u = sum_i c_i f_i           (Sec. 2.3.3)
+ *   equation of state  P(rho) of vdW, PR, RKS or CS                    (Sec. 3.1)
+ *   pseudo-potential   psi = sqrt|P - P0|, P0 = rho/3                   (Sec. 2.3.4, 2.3.5)
+ *   Korteweg force     2-ring isotropic stencils of psi and rho         (Eq. Kforce_final)
+ *   correction Phi     diagonal third-moment correction                 (Eq. correction)
+ *   collision          f + omega (feq - f) + (f* - feq), product form   (Eqs. LBMeq, LBGK, LBMstar)
+ *   streaming          f_i(r + c_i, t + 1) = post_i(r, t); a population
+ *                      headed into a solid node is bounced back halfway
+ *                      into the opposite direction at its origin.
+ * The force enters xi* = u + F/rho as the force acting on the fluid,
+ * F = -s 2 psi S_psi - kappa rho S_rho (the printed Kforce_final is the
+ * momentum-balance term, of opposite sign); zeta* = 1/3 + xi*^2 + Phi/rho;
+ * Phi_aa = -(1 - omega/2) d_a(rho u_a^3) by a central difference.
+ *
+ * Units are lattice units: dr = dt = 1, cs^2 = 1/3, gas constant R = 1.
+ *
+ * Layouts (all arrays row-major with x fastest):
+ *   node index        n = x + nx * (y + ny * z), N = nx * ny * nz nodes
+ *   scalar field      double[N]
+ *   vector field      double[D * N], component a at [a * N + n] (D = 2 or 3)
+ *   populations       double[Q * N], direction i at [i * N + n],
+ *                     i = (cx+1) + 3 (cy+1) [+ 9 (cz+1)], opposite = Q-1-i
+ *   solid mask        uint8_t[N], 1 = solid, 0 = fluid
+ *
+ * Ownership: the library copies every host input and keeps no caller
+ * pointer, except memory passed to lbm_bind_device_memory, which the caller
+ * keeps alive until lbm_destroy. A handle is not thread-safe; all its work
+ * is ordered on one CUDA stream (lbm_set_stream). Device pointers passed
+ * with on_device = 1 must be readable/writable on the handle's device and
+ * stream.
+ *
+ * Errors: every call returns an lbm_status; nothing is thrown across the
+ * ABI. lbm_last_error() gives a message for the last failure of a handle.
+ * A step that produced a non-finite or non-positive density is reported as
+ * LBM_ENONFINITE by the next synchronising call (lbm_sync, lbm_moments,
+ * lbm_reduce, lbm_get_populations); the handle then refuses lbm_step with
+ * LBM_ESTATE until lbm_init or lbm_set_populations.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx *lbm_handle;
+
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q27 = 1 };
+
+/* Equations of state of Sec. 3.1: van der Waals (Eq. vdWEoS), Peng-Robinson
+ * (Eq. PREoS), Redlich-Kwong-Soave (Eq. RKSEoS), Carnahan-Starling (Eq. CSEos). */
+enum lbm_eos { LBM_EOS_VDW = 0, LBM_EOS_PR = 1, LBM_EOS_RKS = 2, LBM_EOS_CS = 3 };
+
+/* Population storage. LBM_F64 stores and computes in FP64. */
+enum lbm_storage { LBM_F64 = 0, LBM_F32 = 1 };
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,      /* bad argument; nothing changed */
+    LBM_ENOMEM = 2,      /* device allocation failed or bound memory too small */
+    LBM_ECUDA = 3,       /* a CUDA call failed; see lbm_last_error */
+    LBM_ENONFINITE = 4,  /* a density became non-finite or <= 0 */
+    LBM_ETIMEOUT = 5,    /* lbm_sync deadline passed; work still in flight */
+    LBM_ESTATE = 6       /* call not valid in the handle's state */
+};
+
+/* Flags of lbm_params.flags. */
+enum { LBM_FLAG_PHI_OFF = 1 /* drop the correction Phi (Eq. correction) */ };
+
+/* EOS constants and options. a, b: EOS attraction and co-volume (lattice
+ * units, R = 1); acentric: acentric factor of PR/RKS (Sec. 3.1); rho_w:
+ * virtual density of solid nodes seen by both force stencils (Sec. 4.5). */
+typedef struct {
+    double a, b, acentric, rho_w;
+    int storage;   /* enum lbm_storage */
+    int flags;     /* LBM_FLAG_* */
+} lbm_params;
+
+/* Fill p with the defaults of an EOS: vdW a = 9/49, b = 2/21; PR and RKS
+ * a = 2/49, b = 2/21; CS a = 1, b = 4; acentric 0.344; rho_w = 1;
+ * LBM_F64; no flags. Returns LBM_EINVAL for an unknown eos. */
+int lbm_default_params(int eos, lbm_params *p);
+
+/* Create a handle for one lattice. lattice: enum lbm_lattice. nx, ny, nz:
+ * lattice size, each >= 5 (the 2-ring stencils must not alias under the
+ * periodic wrap); nz must be 1 for D2Q9. eos: enum lbm_eos. t_over_tc:
+ * reduced temperature, 0 < T/Tc < 1 (T = (T/Tc) Tc, Tc from a and b by the
+ * relations printed under each EOS). kappa: capillary coefficient kappa~ of
+ * Eq. capillary_discrete, >= 0. tau: relaxation time, omega = 1/tau, > 1/2
+ * (kinematic viscosity (tau - 1/2)/3). solid_mask: host uint8_t[N] or NULL
+ * (all fluid); copied. p: NULL for lbm_default_params(eos). Allocates no
+ * device memory; uses the current CUDA device. */
+int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos,
+               double t_over_tc, double kappa, double tau, const uint8_t *solid_mask,
+               const lbm_params *p);
+
+/* Device bytes a handle of this shape and storage needs (populations,
+ * side fields, mask, reduction partials), or 0 for invalid arguments. */
+size_t lbm_required_bytes(int lattice, int nx, int ny, int nz, int storage);
+
+/* Use caller-owned device memory (e.g. a torch tensor) of at least
+ * lbm_required_bytes bytes, 256-byte aligned, instead of allocating.
+ * Must be called before lbm_init. */
+int lbm_bind_device_memory(lbm_handle h, void *dev, size_t bytes);
+
+/* Order all later work of the handle on this cudaStream_t (NULL: the
+ * handle's own stream, created by lbm_create). */
+int lbm_set_stream(lbm_handle h, void *stream);
+
+/* Set populations to the equilibrium f_eq(rho0, u0) (Eq. LBMeq) at fluid
+ * nodes. rho0: double[N] (> 0 at fluid nodes); u0: double[D*N] or NULL
+ * for zero. on_device: 0 if the pointers are host memory, 1 if device.
+ * Allocates the device memory on first use unless bound. */
+int lbm_init(lbm_handle h, const double *rho0, const double *u0, int on_device);
+
+/* Advance n >= 0 time steps. Asynchronous on the handle's stream; steps
+ * after the first are replayed from a CUDA graph of two steps. */
+int lbm_step(lbm_handle h, int64_t n);
+
+/* Macroscopic fields of the current state: rho (double[N]), bare velocity
+ * u = sum c_i f_i / rho (double[D*N]) and the physical velocity
+ * U = u + F/(2 rho) of Sec. 2.3.5 (double[D*N]); any may be NULL. Solid
+ * nodes report rho_w and zero velocities. Synchronises the stream. */
+int lbm_moments(lbm_handle h, double *rho, double *u, double *U, int on_device);
+
+/* Mass sum rho and momentum sum rho u over fluid nodes (host outputs;
+ * momentum has D entries), summed in a fixed order on the device.
+ * Synchronises the stream. */
+int lbm_reduce(lbm_handle h, double *mass, double *momentum);
+
+/* Copy the populations (double[Q*N]) out or in. Solid-node entries read as
+ * 0 and are ignored on input. Synchronising. */
+int lbm_get_populations(lbm_handle h, double *f, int on_device);
+int lbm_set_populations(lbm_handle h, const double *f, int on_device);
+
+/* Wait for the handle's stream at most timeout_ms milliseconds (< 0: no
+ * limit); LBM_ETIMEOUT if work is still running, LBM_ENONFINITE if a step
+ * saw a bad density. */
+int lbm_sync(lbm_handle h, int timeout_ms);
+
+/* Number of kernel launches the handle has issued (graph replays count
+ * each kernel in the graph). */
+int64_t lbm_launch_count(lbm_handle h);
+
+/* Advance n >= 1 steps with plain launches, timing each kernel with CUDA
+ * events on the handle's stream. ms[0] receives the mean duration of the
+ * moments kernel, ms[1] of the collide-and-stream kernel (milliseconds).
+ * Synchronising. */
+int lbm_time_kernels(lbm_handle h, int64_t n, double *ms);
+
+const char *lbm_last_error(lbm_handle h);
+
+void lbm_destroy(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,591 @@
+// C ABI of the two-phase lattice Boltzmann library (declared in include/lbm.h).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+using lbmk::Geo;
+using lbmk::Phys;
+
+struct lbm_ctx {
+    int lattice, D, Q;
+    Geo geo;
+    Phys phys;
+    int storage, flags;
+    double t_over_tc, tau;
+    std::vector<uint8_t> mask_host;
+    int device;
+    cudaStream_t own_stream = nullptr, stream = nullptr, cap_stream = nullptr;
+    // device memory
+    void *base = nullptr;
+    bool owns_base = false;
+    size_t bytes = 0;
+    double *f[2] = {nullptr, nullptr};
+    double2 *rp = nullptr;
+    double *u = nullptr, *gflux = nullptr, *partial = nullptr, *sums = nullptr;
+    uint8_t *mask = nullptr;
+    int *status = nullptr;
+    int cur = 0;
+    bool initialised = false, bad = false;
+    cudaGraphExec_t graph = nullptr;
+    int64_t launches = 0;
+    char err[512] = {0};
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t f0, f1, rp, u, g, mask, partial, sums, status, total;
+};
+
+Layout layout_for(int D, int Q, size_t N)
+{
+    Layout L;
+    size_t o = 0;
+    L.f0 = o; o = align_up(o + sizeof(double) * Q * N);
+    L.f1 = o; o = align_up(o + sizeof(double) * Q * N);
+    L.rp = o; o = align_up(o + sizeof(double2) * N);
+    L.u = o; o = align_up(o + sizeof(double) * D * N);
+    L.g = o; o = align_up(o + sizeof(double) * D * N);
+    L.mask = o; o = align_up(o + N);
+    L.partial = o; o = align_up(o + sizeof(double) * 4 * lbmk::RED_BLOCKS);
+    L.sums = o; o = align_up(o + sizeof(double) * 4);
+    L.status = o; o = align_up(o + sizeof(int) * 4);
+    L.total = o;
+    return L;
+}
+
+bool valid_shape(int lattice, int nx, int ny, int nz)
+{
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return false;
+    if (nx < 5 || ny < 5) return false;
+    if (lattice == LBM_D2Q9 && nz != 1) return false;
+    if (lattice == LBM_D3Q27 && nz < 5) return false;
+    // 32-bit node indices in the kernels
+    if ((double)nx * ny * nz * 27.0 > 4.0e9) return false;
+    return true;
+}
+
+int fail(lbm_ctx *h, int code, const char *fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CU(h, call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail((h), LBM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+double eos_rtc(int eos, double a, double b)
+{
+    switch (eos) {
+    case LBM_EOS_VDW: return 8.0 * a / (27.0 * b);
+    case LBM_EOS_PR: return (0.0778 / 0.45724) * a / b;
+    case LBM_EOS_RKS: return (0.08664 / 0.42748) * a / b;
+    case LBM_EOS_CS: return (0.18727 / 0.4963) * a / b;
+    }
+    return NAN;
+}
+
+double eos_alpha(int eos, double acentric, double tr)
+{
+    double m;
+    if (eos == LBM_EOS_PR) m = 0.37464 + 1.54226 * acentric - 0.26992 * acentric * acentric;
+    else if (eos == LBM_EOS_RKS) m = 0.480 + 1.574 * acentric - 0.176 * acentric * acentric;
+    else return 1.0;
+    const double s = 1.0 + m * (1.0 - std::sqrt(tr));
+    return s * s;
+}
+
+dim3 node_block(const Geo &g)
+{
+    int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
+    return dim3(bx, 1, 1);
+}
+
+dim3 node_grid(const Geo &g)
+{
+    dim3 b = node_block(g);
+    return dim3((g.nx + b.x - 1) / b.x, g.ny, g.nz);
+}
+
+int ensure_memory(lbm_ctx *h)
+{
+    if (h->f[0]) return LBM_OK;
+    Layout L = layout_for(h->D, h->Q, h->geo.N);
+    if (!h->base) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, LBM_ENOMEM, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+        }
+        h->base = p;
+        h->owns_base = true;
+        h->bytes = L.total;
+    }
+    char *b = static_cast<char *>(h->base);
+    h->f[0] = reinterpret_cast<double *>(b + L.f0);
+    h->f[1] = reinterpret_cast<double *>(b + L.f1);
+    h->rp = reinterpret_cast<double2 *>(b + L.rp);
+    h->u = reinterpret_cast<double *>(b + L.u);
+    h->gflux = reinterpret_cast<double *>(b + L.g);
+    h->mask = reinterpret_cast<uint8_t *>(b + L.mask);
+    h->partial = reinterpret_cast<double *>(b + L.partial);
+    h->sums = reinterpret_cast<double *>(b + L.sums);
+    h->status = reinterpret_cast<int *>(b + L.status);
+    CU(h, cudaMemcpyAsync(h->mask, h->mask_host.data(), h->geo.N, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+template <int LAT>
+int launch_step(lbm_ctx *h, cudaStream_t s)
+{
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    const double *src = h->f[h->cur];
+    double *dst = h->f[h->cur ^ 1];
+    lbmk::k_macro<LAT><<<gr, bl, 0, s>>>(h->geo, h->phys, h->mask, src, h->rp, h->u, h->gflux,
+                                         h->status);
+    lbmk::k_collide<LAT><<<gr, bl, 0, s>>>(h->geo, h->phys, h->mask, src, dst, h->rp, h->u,
+                                           h->gflux);
+    CU(h, cudaGetLastError());
+    h->cur ^= 1;
+    return LBM_OK;
+}
+
+int step_plain(lbm_ctx *h, cudaStream_t s)
+{
+    int rc = h->lattice == LBM_D2Q9 ? launch_step<0>(h, s) : launch_step<1>(h, s);
+    if (rc == LBM_OK) h->launches += 2;
+    return rc;
+}
+
+// Two steps (state buffer 0 -> 1 -> 0) captured once on the library's own
+// stream; replayed on the handle's stream.
+int ensure_graph(lbm_ctx *h)
+{
+    if (h->graph) return LBM_OK;
+    if (!h->cap_stream) CU(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int saved = h->cur;
+    int rc = step_plain(h, h->cap_stream);
+    if (rc == LBM_OK) rc = step_plain(h, h->cap_stream);
+    h->launches -= 4;  // captured, not launched
+    h->cur = saved;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+int read_status(lbm_ctx *h)
+{
+    int st = 0;
+    CU(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (st) {
+        h->bad = true;
+        return fail(h, LBM_ENONFINITE, "a density became non-finite or non-positive");
+    }
+    return LBM_OK;
+}
+
+int check_ready(lbm_ctx *h)
+{
+    if (!h) return LBM_EINVAL;
+    if (!h->initialised) return fail(h, LBM_ESTATE, "handle not initialised (call lbm_init)");
+    return LBM_OK;
+}
+
+template <int LAT>
+int launch_macro_and_out(lbm_ctx *h, double *rho, double *u, double *U)
+{
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    lbmk::k_macro<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->f[h->cur], h->rp,
+                                                 h->u, h->gflux, h->status);
+    lbmk::k_moments_out<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
+                                                       rho, u, U);
+    CU(h, cudaGetLastError());
+    h->launches += 2;
+    return LBM_OK;
+}
+
+template <int LAT>
+int launch_init(lbm_ctx *h, const double *rho0, const double *u0)
+{
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0, h->f[h->cur]);
+    lbmk::k_fill_solid<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
+                                                      h->gflux);
+    CU(h, cudaGetLastError());
+    h->launches += 2;
+    return LBM_OK;
+}
+
+template <int LAT>
+int launch_fill_solid(lbm_ctx *h)
+{
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    lbmk::k_fill_solid<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
+                                                      h->gflux);
+    CU(h, cudaGetLastError());
+    h->launches += 1;
+    return LBM_OK;
+}
+
+template <int LAT>
+int launch_reduce(lbm_ctx *h)
+{
+    lbmk::k_reduce_partial<LAT><<<lbmk::RED_BLOCKS, lbmk::RED_THREADS, 0, h->stream>>>(
+        h->geo, h->mask, h->f[h->cur], h->partial);
+    lbmk::k_reduce_final<<<1, lbmk::RED_BLOCKS, 0, h->stream>>>(h->partial, h->sums);
+    CU(h, cudaGetLastError());
+    h->launches += 2;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_default_params(int eos, lbm_params *p)
+{
+    if (!p) return LBM_EINVAL;
+    switch (eos) {
+    case LBM_EOS_VDW: p->a = 9.0 / 49.0; p->b = 2.0 / 21.0; break;
+    case LBM_EOS_PR:
+    case LBM_EOS_RKS: p->a = 2.0 / 49.0; p->b = 2.0 / 21.0; break;
+    case LBM_EOS_CS: p->a = 1.0; p->b = 4.0; break;
+    default: return LBM_EINVAL;
+    }
+    p->acentric = 0.344;
+    p->rho_w = 1.0;
+    p->storage = LBM_F64;
+    p->flags = 0;
+    return LBM_OK;
+}
+
+size_t lbm_required_bytes(int lattice, int nx, int ny, int nz, int storage)
+{
+    if (!valid_shape(lattice, nx, ny, nz) || storage != LBM_F64) return 0;
+    const int D = lattice == LBM_D2Q9 ? 2 : 3, Q = lattice == LBM_D2Q9 ? 9 : 27;
+    return layout_for(D, Q, (size_t)nx * ny * nz).total;
+}
+
+int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, double t_over_tc,
+               double kappa, double tau, const uint8_t *solid_mask, const lbm_params *p)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (!valid_shape(lattice, nx, ny, nz)) return LBM_EINVAL;
+    if (eos < LBM_EOS_VDW || eos > LBM_EOS_CS) return LBM_EINVAL;
+    if (!(t_over_tc > 0.0 && t_over_tc < 1.0) || !(kappa >= 0.0) || !(tau > 0.5)) return LBM_EINVAL;
+    lbm_params prm;
+    if (p) prm = *p;
+    else lbm_default_params(eos, &prm);
+    if (prm.storage != LBM_F64) return LBM_EINVAL;
+    if (!(prm.a > 0.0) || !(prm.b > 0.0) || !(prm.rho_w > 0.0)) return LBM_EINVAL;
+    lbm_ctx *h = new (std::nothrow) lbm_ctx();
+    if (!h) return LBM_ENOMEM;
+    h->lattice = lattice;
+    h->D = lattice == LBM_D2Q9 ? 2 : 3;
+    h->Q = lattice == LBM_D2Q9 ? 9 : 27;
+    h->geo.nx = nx; h->geo.ny = ny; h->geo.nz = nz;
+    h->geo.N = (unsigned)((size_t)nx * ny * nz);
+    h->storage = prm.storage;
+    h->flags = prm.flags;
+    h->t_over_tc = t_over_tc;
+    h->tau = tau;
+    Phys &ph = h->phys;
+    ph.eos = eos;
+    ph.a = prm.a;
+    ph.b = prm.b;
+    ph.RT = t_over_tc * eos_rtc(eos, prm.a, prm.b);
+    ph.alpha = eos_alpha(eos, prm.acentric, t_over_tc);
+    ph.kappa = kappa;
+    ph.omega = 1.0 / tau;
+    ph.phi_pref = (prm.flags & LBM_FLAG_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * ph.omega);
+    ph.rho_w = prm.rho_w;
+    h->mask_host.assign(h->geo.N, 0);
+    if (solid_mask)
+        for (size_t n = 0; n < h->geo.N; ++n) h->mask_host[n] = solid_mask[n] ? 1 : 0;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return LBM_ECUDA;
+    }
+    h->stream = h->own_stream;
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_bind_device_memory(lbm_handle h, void *dev, size_t bytes)
+{
+    if (!h || !dev) return LBM_EINVAL;
+    if (h->f[0]) return fail(h, LBM_ESTATE, "device memory already in use");
+    if (reinterpret_cast<uintptr_t>(dev) % kAlign) return fail(h, LBM_EINVAL, "memory not 256-byte aligned");
+    const size_t need = layout_for(h->D, h->Q, h->geo.N).total;
+    if (bytes < need) return fail(h, LBM_ENOMEM, "bound memory %zu < required %zu", bytes, need);
+    h->base = dev;
+    h->owns_base = false;
+    h->bytes = bytes;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle h, void *stream)
+{
+    if (!h) return LBM_EINVAL;
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_handle h, const double *rho0, const double *u0, int on_device)
+{
+    if (!h || !rho0) return LBM_EINVAL;
+    int rc = ensure_memory(h);
+    if (rc) return rc;
+    const size_t N = h->geo.N;
+    h->cur = 0;
+    const double *r = rho0, *v = u0;
+    if (!on_device) {
+        // stage through the second population buffer, dead between steps
+        double *st = h->f[1];
+        CU(h, cudaMemcpyAsync(st, rho0, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+        r = st;
+        if (u0) {
+            CU(h, cudaMemcpyAsync(st + N, u0, sizeof(double) * h->D * N, cudaMemcpyHostToDevice,
+                                  h->stream));
+            v = st + N;
+        }
+    }
+    CU(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    rc = h->lattice == LBM_D2Q9 ? launch_init<0>(h, r, v) : launch_init<1>(h, r, v);
+    if (rc) return rc;
+    CU(h, cudaStreamSynchronize(h->stream));
+    h->initialised = true;
+    h->bad = false;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, int64_t n)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (n < 0) return fail(h, LBM_EINVAL, "negative step count");
+    if (h->bad) return fail(h, LBM_ESTATE, "state holds a non-finite density; re-initialise");
+    if (n >= 4) {
+        if (h->cur != 0) {
+            if ((rc = step_plain(h, h->stream))) return rc;
+            --n;
+        }
+        if ((rc = ensure_graph(h))) return rc;
+        for (int64_t k = 0; k < n / 2; ++k) {
+            CU(h, cudaGraphLaunch(h->graph, h->stream));
+            h->launches += 4;
+        }
+        n %= 2;
+    }
+    for (int64_t k = 0; k < n; ++k)
+        if ((rc = step_plain(h, h->stream))) return rc;
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle h, double *rho, double *u, double *U, int on_device)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    const size_t N = h->geo.N, D = h->D;
+    double *dr = rho, *du = u, *dU = U;
+    if (!on_device) {
+        double *st = h->f[h->cur ^ 1];  // dead between steps
+        dr = rho ? st : nullptr;
+        du = u ? st + N : nullptr;
+        dU = U ? st + N + D * N : nullptr;
+    }
+    rc = h->lattice == LBM_D2Q9 ? launch_macro_and_out<0>(h, dr, du, dU)
+                                : launch_macro_and_out<1>(h, dr, du, dU);
+    if (rc) return rc;
+    if (!on_device) {
+        if (rho) CU(h, cudaMemcpyAsync(rho, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+        if (u) CU(h, cudaMemcpyAsync(u, du, sizeof(double) * D * N, cudaMemcpyDeviceToHost, h->stream));
+        if (U) CU(h, cudaMemcpyAsync(U, dU, sizeof(double) * D * N, cudaMemcpyDeviceToHost, h->stream));
+    }
+    return read_status(h);
+}
+
+int lbm_reduce(lbm_handle h, double *mass, double *momentum)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (!mass && !momentum) return LBM_EINVAL;
+    rc = h->lattice == LBM_D2Q9 ? launch_reduce<0>(h) : launch_reduce<1>(h);
+    if (rc) return rc;
+    double s[4];
+    CU(h, cudaMemcpyAsync(s, h->sums, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    rc = read_status(h);  // synchronises
+    if (mass) *mass = s[0];
+    if (momentum)
+        for (int a = 0; a < h->D; ++a) momentum[a] = s[1 + a];
+    return rc;
+}
+
+int lbm_get_populations(lbm_handle h, double *f, int on_device)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (!f) return LBM_EINVAL;
+    const size_t N = h->geo.N, QN = (size_t)h->Q * N;
+    CU(h, cudaMemcpyAsync(f, h->f[h->cur], sizeof(double) * QN,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    rc = read_status(h);
+    if (!on_device)
+        for (size_t n = 0; n < N; ++n)
+            if (h->mask_host[n])
+                for (int i = 0; i < h->Q; ++i) f[(size_t)i * N + n] = 0.0;
+    return rc;
+}
+
+int lbm_set_populations(lbm_handle h, const double *f, int on_device)
+{
+    if (!h || !f) return LBM_EINVAL;
+    int rc = ensure_memory(h);
+    if (rc) return rc;
+    const size_t QN = (size_t)h->Q * h->geo.N;
+    h->cur = 0;
+    CU(h, cudaMemcpyAsync(h->f[0], f, sizeof(double) * QN,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    rc = h->lattice == LBM_D2Q9 ? launch_fill_solid<0>(h) : launch_fill_solid<1>(h);
+    if (rc) return rc;
+    CU(h, cudaStreamSynchronize(h->stream));
+    h->initialised = true;
+    h->bad = false;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle h, int timeout_ms)
+{
+    if (!h) return LBM_EINVAL;
+    if (!h->initialised) return LBM_OK;
+    if (timeout_ms >= 0) {
+        cudaEvent_t ev;
+        CU(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, h->stream);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(ev);
+            return fail(h, LBM_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+        }
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            e = cudaEventQuery(ev);
+            if (e != cudaErrorNotReady) break;
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) {
+                cudaEventDestroy(ev);
+                return fail(h, LBM_ETIMEOUT, "work still running after %d ms", timeout_ms);
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return fail(h, LBM_ECUDA, "stream error: %s", cudaGetErrorString(e));
+    }
+    return read_status(h);
+}
+
+int64_t lbm_launch_count(lbm_handle h) { return h ? h->launches : -1; }
+
+int lbm_time_kernels(lbm_handle h, int64_t n, double *ms)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (n < 1 || !ms) return fail(h, LBM_EINVAL, "need n >= 1 and an output array");
+    if (h->bad) return fail(h, LBM_ESTATE, "state holds a non-finite density; re-initialise");
+    std::vector<cudaEvent_t> ev(3 * n);
+    for (auto &e : ev) CU(h, cudaEventCreate(&e));
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    for (int64_t k = 0; k < n; ++k) {
+        const double *src = h->f[h->cur];
+        double *dst = h->f[h->cur ^ 1];
+        CU(h, cudaEventRecord(ev[3 * k], h->stream));
+        if (h->lattice == LBM_D2Q9)
+            lbmk::k_macro<0><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, h->rp, h->u,
+                                                       h->gflux, h->status);
+        else
+            lbmk::k_macro<1><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, h->rp, h->u,
+                                                       h->gflux, h->status);
+        CU(h, cudaEventRecord(ev[3 * k + 1], h->stream));
+        if (h->lattice == LBM_D2Q9)
+            lbmk::k_collide<0><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, dst, h->rp,
+                                                         h->u, h->gflux);
+        else
+            lbmk::k_collide<1><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, dst, h->rp,
+                                                         h->u, h->gflux);
+        CU(h, cudaEventRecord(ev[3 * k + 2], h->stream));
+        CU(h, cudaGetLastError());
+        h->cur ^= 1;
+        h->launches += 2;
+    }
+    CU(h, cudaStreamSynchronize(h->stream));
+    double t0 = 0.0, t1 = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        float a = 0.f, b = 0.f;
+        CU(h, cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]));
+        CU(h, cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]));
+        t0 += a;
+        t1 += b;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    ms[0] = t0 / n;
+    ms[1] = t1 / n;
+    return read_status(h);
+}
+
+const char *lbm_last_error(lbm_handle h) { return h ? h->err : "null handle"; }
+
+void lbm_destroy(lbm_handle h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->owns_base && h->base) cudaFree(h->base);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // extern "C"

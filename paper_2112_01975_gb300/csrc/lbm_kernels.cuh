@@ -1,0 +1,392 @@
+// Device code of the two-phase lattice Boltzmann step (arXiv 2112.01975).
+//
+// Storage: populations SoA f[i * N + n] (FP64), node n = x + nx (y + ny z);
+// side fields written once per step by k_macro and read by k_collide:
+//   rp[n] = (rho, s psi)   double2; s = +1 where P > P0, else -1 (Sec. 2.3.4)
+//   u[a * N + n]           bare velocity sum c f / rho (Sec. 2.3.3)
+//   g[a * N + n]           rho u_a^3, the flux differenced by Phi (Eq. correction)
+// Solid nodes hold the virtual density rho_w, u = g = 0 (written at init).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+struct Geo {
+    int nx, ny, nz;
+    unsigned N;
+};
+
+struct Phys {
+    int eos;
+    double a, b, RT, alpha;   // EOS constants at the run's temperature (R = 1)
+    double kappa;             // capillary coefficient kappa~
+    double omega;             // 1 / tau
+    double phi_pref;          // -(1 - omega/2), or 0 with the correction off
+    double rho_w;             // virtual solid density
+};
+
+template <int LAT> struct Lattice;
+template <> struct Lattice<0> { static constexpr int D = 2, Q = 9; };
+template <> struct Lattice<1> { static constexpr int D = 3, Q = 27; };
+
+__host__ __device__ constexpr int cxi(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cyi(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int czi(int i) { return i / 9 - 1; }
+
+// Pressure of the equations of state of Sec. 3.1 (gas constant 1).
+__device__ __forceinline__ double eos_pressure(const Phys &p, double rho)
+{
+    const double rep = rho * p.RT / (1.0 - p.b * rho);
+    switch (p.eos) {
+    case 0:  // van der Waals
+        return rep - p.a * rho * rho;
+    case 1:  // Peng-Robinson
+        return rep - p.a * p.alpha * rho * rho / (1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho);
+    case 2:  // Redlich-Kwong-Soave
+        return rep - p.a * p.alpha * rho * rho / (1.0 + p.b * rho);
+    default: {  // Carnahan-Starling
+        const double e = 0.25 * p.b * rho;
+        const double om = 1.0 - e;
+        return rho * p.RT * (1.0 + e + e * e - e * e * e) / (om * om * om) - p.a * rho * rho;
+    }
+    }
+}
+
+// Signed pseudo-potential s psi with psi = sqrt|P - P0|, P0 = rho/3.
+__device__ __forceinline__ double signed_psi(const Phys &p, double rho)
+{
+    const double d = eos_pressure(p, rho) - rho * (1.0 / 3.0);
+    return d > 0.0 ? sqrt(d) : -sqrt(-d);
+}
+
+__device__ __forceinline__ int wrapm(int v, int n) { return v < 0 ? v + n : v; }
+__device__ __forceinline__ int wrapp(int v, int n) { return v >= n ? v - n : v; }
+
+// Korteweg force acting on the fluid at one node:
+//   F = -2 (s psi)_c S_psi - kappa rho_c S_rho,
+//   S_psi = sum_i (w_i/cs2) c_i [4/3 psi(r+c_i) - 1/6 psi(r+2c_i)],
+//   S_rho = sum_i (w_i/cs2) c_i [2 rho(r+c_i) - rho(r+2c_i)]   (Eq. Kforce_final).
+// w_i/cs2 c_ia = 1/2 W(c_ib) W(c_ic) c_ia with the 1D weights W(0) = 2/3,
+// W(+-1) = 1/6 of Eq. wi, so each ring sums neighbours by their number of
+// nonzero transverse components (centre, edge, corner) before weighting.
+template <int LAT>
+__device__ __forceinline__ void korteweg_force(const Geo &g, const Phys &p,
+                                               const double2 *__restrict__ rp, int x, int y,
+                                               int z, double rho_c, double spsi_c, double *F)
+{
+    constexpr int D = Lattice<LAT>::D;
+    double Spsi[3] = {0.0, 0.0, 0.0}, Srho[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int s = 1; s <= 2; ++s) {
+        const int xm = wrapm(x - s, g.nx), xp = wrapp(x + s, g.nx);
+        const int ym = wrapm(y - s, g.ny), yp = wrapp(y + s, g.ny);
+        int zm = 0, zp = 0;
+        if (D == 3) { zm = wrapm(z - s, g.nz); zp = wrapp(z + s, g.nz); }
+        const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
+        double ap[3][3], ar[3][3];  // [component][0 centre, 1 edge, 2 corner]
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { ap[a][k] = 0.0; ar[a][k] = 0.0; }
+#pragma unroll
+        for (int i = 0; i < Lattice<LAT>::Q; ++i) {
+            const int c[3] = {cxi(i), cyi(i), D == 3 ? czi(i) : 0};
+            if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
+            const unsigned nb = X[c[0] + 1] + g.nx * (Y[c[1] + 1] + g.ny * Z[c[2] + 1]);
+            const double2 v = rp[nb];
+            const double ps = fabs(v.y);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                if (c[a] == 0) continue;
+                const int k = (a != 0 && c[0] != 0) + (a != 1 && c[1] != 0) + (a != 2 && c[2] != 0);
+                if (c[a] > 0) { ap[a][k] += ps; ar[a][k] += v.x; }
+                else          { ap[a][k] -= ps; ar[a][k] -= v.x; }
+            }
+        }
+        const double gp = s == 1 ? 4.0 / 3.0 : -1.0 / 6.0;
+        const double gr = s == 1 ? 2.0 : -1.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double dp, dr;
+            if (D == 3) {
+                dp = (2.0 / 9.0) * ap[a][0] + (1.0 / 18.0) * ap[a][1] + (1.0 / 72.0) * ap[a][2];
+                dr = (2.0 / 9.0) * ar[a][0] + (1.0 / 18.0) * ar[a][1] + (1.0 / 72.0) * ar[a][2];
+            } else {
+                dp = (1.0 / 3.0) * ap[a][0] + (1.0 / 12.0) * ap[a][1];
+                dr = (1.0 / 3.0) * ar[a][0] + (1.0 / 12.0) * ar[a][1];
+            }
+            Spsi[a] += gp * dp;
+            Srho[a] += gr * dr;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) F[a] = -2.0 * spsi_c * Spsi[a] - p.kappa * rho_c * Srho[a];
+}
+
+// Moments, EOS and pseudo-potential of every fluid node; flags bad densities.
+template <int LAT>
+__global__ void k_macro(Geo g, Phys p, const uint8_t *__restrict__ mask,
+                        const double *__restrict__ f, double2 *__restrict__ rp,
+                        double *__restrict__ u, double *__restrict__ gflux,
+                        int *__restrict__ status)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+    if (mask[n]) return;
+    // Row sums along x for each (cy, cz), then the moments from them.
+    double fi[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fi[i] = f[(size_t)i * g.N + n];
+    constexpr int R = Q / 3;
+    double row[R], jx = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        row[r] = fi[3 * r] + fi[3 * r + 1] + fi[3 * r + 2];
+        jx += fi[3 * r + 2] - fi[3 * r];
+    }
+    double rho = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        rho += row[r];
+        const int cy = r % 3 - 1, cz = r / 3 - 1;
+        if (cy > 0) jy += row[r]; else if (cy < 0) jy -= row[r];
+        if (D == 3) { if (cz > 0) jz += row[r]; else if (cz < 0) jz -= row[r]; }
+    }
+    const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    if (!(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz))
+        atomicOr(status, 1);
+    rp[n] = make_double2(rho, signed_psi(p, rho));
+    u[n] = ux;
+    u[g.N + n] = uy;
+    gflux[n] = rho * ux * ux * ux;
+    gflux[g.N + n] = rho * uy * uy * uy;
+    if (D == 3) {
+        u[2 * g.N + n] = uz;
+        gflux[2 * g.N + n] = rho * uz * uz * uz;
+    }
+}
+
+// Force, correction, product-form collision and push streaming with
+// halfway bounce-back, one fluid node per thread (Eqs. LBGK, LBMeq, LBMstar).
+template <int LAT>
+__global__ void k_collide(Geo g, Phys p, const uint8_t *__restrict__ mask,
+                          const double *__restrict__ f, double *__restrict__ fout,
+                          const double2 *__restrict__ rp, const double *__restrict__ u,
+                          const double *__restrict__ gflux)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+    if (mask[n]) return;
+    const double2 c = rp[n];
+    const double rho = c.x;
+    double F[3] = {0.0, 0.0, 0.0};
+    korteweg_force<LAT>(g, p, rp, x, y, z, rho, c.y, F);
+    // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2
+    const int xm = wrapm(x - 1, g.nx), xp = wrapp(x + 1, g.nx);
+    const int ym = wrapm(y - 1, g.ny), yp = wrapp(y + 1, g.ny);
+    double Phi[3];
+    Phi[0] = p.phi_pref * 0.5 * (gflux[xp + g.nx * (y + g.ny * z)] - gflux[xm + g.nx * (y + g.ny * z)]);
+    Phi[1] = p.phi_pref * 0.5 * (gflux[g.N + x + g.nx * (yp + g.ny * z)] -
+                                 gflux[g.N + x + g.nx * (ym + g.ny * z)]);
+    int zm = 0, zp = 0;
+    if (D == 3) {
+        zm = wrapm(z - 1, g.nz);
+        zp = wrapp(z + 1, g.nz);
+        Phi[2] = p.phi_pref * 0.5 * (gflux[2 * g.N + x + g.nx * (y + g.ny * zp)] -
+                                     gflux[2 * g.N + x + g.nx * (y + g.ny * zm)]);
+    }
+    // Product-form factors: equilibrium (xi = u, zeta = 1/3 + u^2) and
+    // extended (xi* = u + F/rho, zeta* = 1/3 + xi*^2 + Phi/rho).
+    const double inv_rho = 1.0 / rho;
+    double E[3][3], S[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double ua = u[a * g.N + n];
+        const double ze = 1.0 / 3.0 + ua * ua;
+        E[a][0] = 0.5 * (ze - ua);
+        E[a][1] = 1.0 - ze;
+        E[a][2] = 0.5 * (ze + ua);
+        const double xs = ua + F[a] * inv_rho;
+        const double zs = 1.0 / 3.0 + xs * xs + Phi[a] * inv_rho;
+        S[a][0] = 0.5 * (zs - xs);
+        S[a][1] = 1.0 - zs;
+        S[a][2] = 0.5 * (zs + xs);
+    }
+    const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
+    const double om = p.omega;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cxi(i), cy = cyi(i), cz = D == 3 ? czi(i) : 0;
+        double eq = rho * E[0][cx + 1] * E[1][cy + 1];
+        double st = rho * S[0][cx + 1] * S[1][cy + 1];
+        if (D == 3) { eq *= E[2][cz + 1]; st *= S[2][cz + 1]; }
+        const double fi = f[(size_t)i * g.N + n];
+        const double post = fi + om * (eq - fi) + (st - eq);
+        const unsigned dst = X[cx + 1] + g.nx * (Y[cy + 1] + g.ny * Z[cz + 1]);
+        if (mask[dst]) fout[(size_t)(Q - 1 - i) * g.N + n] = post;
+        else           fout[(size_t)i * g.N + dst] = post;
+    }
+}
+
+// Output moments: rho, bare u and U = u + F/(2 rho) (Sec. 2.3.5).
+template <int LAT>
+__global__ void k_moments_out(Geo g, Phys p, const uint8_t *__restrict__ mask,
+                              const double2 *__restrict__ rp, const double *__restrict__ u,
+                              double *__restrict__ rho_out, double *__restrict__ u_out,
+                              double *__restrict__ U_out)
+{
+    constexpr int D = Lattice<LAT>::D;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+    if (mask[n]) {
+        if (rho_out) rho_out[n] = p.rho_w;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            if (u_out) u_out[a * g.N + n] = 0.0;
+            if (U_out) U_out[a * g.N + n] = 0.0;
+        }
+        return;
+    }
+    const double2 c = rp[n];
+    double F[3] = {0.0, 0.0, 0.0};
+    if (U_out) korteweg_force<LAT>(g, p, rp, x, y, z, c.x, c.y, F);
+    if (rho_out) rho_out[n] = c.x;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double ua = u[a * g.N + n];
+        if (u_out) u_out[a * g.N + n] = ua;
+        if (U_out) U_out[a * g.N + n] = ua + F[a] / (2.0 * c.x);
+    }
+}
+
+// Equilibrium populations from (rho0, u0) at fluid nodes, zero at solid nodes;
+// solid nodes' side fields get rho_w and zero velocity.
+template <int LAT>
+__global__ void k_init(Geo g, Phys p, const uint8_t *__restrict__ mask,
+                       const double *__restrict__ rho0, const double *__restrict__ u0,
+                       double *__restrict__ f)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+    if (mask[n]) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[(size_t)i * g.N + n] = 0.0;
+        return;
+    }
+    const double rho = rho0[n];
+    double E[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double ua = u0 ? u0[a * g.N + n] : 0.0;
+        const double ze = 1.0 / 3.0 + ua * ua;
+        E[a][0] = 0.5 * (ze - ua);
+        E[a][1] = 1.0 - ze;
+        E[a][2] = 0.5 * (ze + ua);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        double eq = rho * E[0][cxi(i) + 1] * E[1][cyi(i) + 1];
+        if (D == 3) eq *= E[2][czi(i) + 1];
+        f[(size_t)i * g.N + n] = eq;
+    }
+}
+
+template <int LAT>
+__global__ void k_fill_solid(Geo g, Phys p, const uint8_t *__restrict__ mask,
+                             double2 *__restrict__ rp, double *__restrict__ u,
+                             double *__restrict__ gflux)
+{
+    constexpr int D = Lattice<LAT>::D;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+    if (!mask[n]) return;
+    rp[n] = make_double2(p.rho_w, signed_psi(p, p.rho_w));
+#pragma unroll
+    for (int a = 0; a < D; ++a) { u[a * g.N + n] = 0.0; gflux[a * g.N + n] = 0.0; }
+}
+
+// Mass and momentum: fixed grid, fixed per-thread stride order and a fixed
+// shuffle tree, so the sums are bitwise reproducible run to run.
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 1024;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int LAT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_reduce_partial(Geo g, const uint8_t *__restrict__ mask, const double *__restrict__ f,
+                 double *__restrict__ partial)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned n = blockIdx.x * RED_THREADS + threadIdx.x; n < g.N;
+         n += RED_THREADS * RED_BLOCKS) {
+        if (mask[n]) continue;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double fi = f[(size_t)i * g.N + n];
+            acc[0] += fi;
+            if (cxi(i)) acc[1] += cxi(i) * fi;
+            if (cyi(i)) acc[2] += cyi(i) * fi;
+            if (D == 3 && czi(i)) acc[3] += czi(i) * fi;
+        }
+    }
+    __shared__ double sh[4][RED_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double v = lane < RED_THREADS / 32 ? sh[k][lane] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) partial[4 * blockIdx.x + k] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RED_BLOCKS)
+k_reduce_final(const double *__restrict__ partial, double *__restrict__ out)
+{
+    __shared__ double sh[4][RED_BLOCKS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum(partial[4 * threadIdx.x + k]);
+        if (lane == 0) sh[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double v = warp_sum(sh[k][lane]);
+            if (lane == 0) out[k] = v;
+        }
+    }
+}
+
+}  // namespace lbmk

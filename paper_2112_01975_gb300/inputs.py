@@ -171,4 +171,9 @@ DROP_D3Q27_128 = Workload("d3q27_drop_128^3_pr_tr0.7", 1, 128, 128, 128, 1, 0.7,
                           rho_l=8.08032155174, radius=24.0, seed=2,
                           a=2.0 / 245.0, b=2.0 / 21.0, steps=20000)
 
-WORKLOADS = {w.name: w for w in (DROP_D2Q9_64, DROP_D3Q27_128)}
+# The same drop at 96^3 (radius 18): a smaller case for profiler captures,
+# still larger than L2 (2 x 191 MB of populations).
+DROP_D3Q27_96 = dataclasses.replace(DROP_D3Q27_128, name="d3q27_drop_96^3_pr_tr0.7", nx=96,
+                                    ny=96, nz=96, radius=18.0)
+
+WORKLOADS = {w.name: w for w in (DROP_D2Q9_64, DROP_D3Q27_128, DROP_D3Q27_96)}

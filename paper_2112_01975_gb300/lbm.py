@@ -1,0 +1,232 @@
+"""Python binding of liblbm.so (the C ABI declared in include/lbm.h).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels. PyTorch supplies device memory (a uint8 tensor bound with
+``lbm_bind_device_memory``) and the CUDA stream. There is no CPU fallback:
+if the compiled library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+
+D2Q9, D3Q27 = 0, 1
+EOS_VDW, EOS_PR, EOS_RKS, EOS_CS = 0, 1, 2, 3
+F64, F32 = 0, 1
+FLAG_PHI_OFF = 1
+STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
+          5: "LBM_ETIMEOUT", 6: "LBM_ESTATE"}
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("acentric", C.c_double),
+                ("rho_w", C.c_double), ("storage", C.c_int), ("flags", C.c_int)]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+    L.lbm_default_params.argtypes = [C.c_int, C.POINTER(lbm_params)]
+    L.lbm_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                             C.c_double, C.c_double, C.c_double, vp, C.POINTER(lbm_params)]
+    L.lbm_required_bytes.restype = C.c_size_t
+    L.lbm_required_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.lbm_bind_device_memory.argtypes = [vp, vp, C.c_size_t]
+    L.lbm_set_stream.argtypes = [vp, vp]
+    L.lbm_init.argtypes = [vp, vp, vp, C.c_int]
+    L.lbm_step.argtypes = [vp, i64]
+    L.lbm_moments.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.lbm_reduce.argtypes = [vp, dp, dp]
+    L.lbm_get_populations.argtypes = [vp, vp, C.c_int]
+    L.lbm_set_populations.argtypes = [vp, vp, C.c_int]
+    L.lbm_sync.argtypes = [vp, C.c_int]
+    L.lbm_launch_count.restype = i64
+    L.lbm_launch_count.argtypes = [vp]
+    L.lbm_time_kernels.argtypes = [vp, i64, dp]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    return L
+
+
+_lib = _load()
+# The C functions under their own names, for callers that marshal themselves.
+lbm_default_params = _lib.lbm_default_params
+lbm_create = _lib.lbm_create
+lbm_required_bytes = _lib.lbm_required_bytes
+lbm_bind_device_memory = _lib.lbm_bind_device_memory
+lbm_set_stream = _lib.lbm_set_stream
+lbm_init = _lib.lbm_init
+lbm_step = _lib.lbm_step
+lbm_moments = _lib.lbm_moments
+lbm_reduce = _lib.lbm_reduce
+lbm_get_populations = _lib.lbm_get_populations
+lbm_set_populations = _lib.lbm_set_populations
+lbm_sync = _lib.lbm_sync
+lbm_launch_count = _lib.lbm_launch_count
+lbm_time_kernels = _lib.lbm_time_kernels
+lbm_last_error = _lib.lbm_last_error
+lbm_destroy = _lib.lbm_destroy
+
+
+def default_params(eos: int) -> lbm_params:
+    p = lbm_params()
+    rc = _lib.lbm_default_params(eos, C.byref(p))
+    if rc:
+        raise LBMError(rc, "unknown eos")
+    return p
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+class LBM:
+    """One lattice on the GPU behind the C ABI.
+
+    Host arrays (numpy float64) and device tensors (torch float64 on the
+    handle's device) are both accepted where the C ABI takes ``on_device``.
+    """
+
+    def __init__(self, lattice: int, nx: int, ny: int, nz: int, eos: int, t_over_tc: float,
+                 kappa: float, tau: float, mask=None, a: float | None = None,
+                 b: float | None = None, acentric: float | None = None,
+                 rho_w: float | None = None, flags: int = 0, storage: int = F64,
+                 stream=None, torch_memory: bool = True):
+        import torch
+        self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
+        self.D = 2 if lattice == D2Q9 else 3
+        self.Q = 9 if lattice == D2Q9 else 27
+        self.N = nx * ny * nz
+        p = default_params(eos)
+        if a is not None:
+            p.a = a
+        if b is not None:
+            p.b = b
+        if acentric is not None:
+            p.acentric = acentric
+        if rho_w is not None:
+            p.rho_w = rho_w
+        p.flags = flags
+        p.storage = storage
+        self.params = p
+        mptr = None
+        if mask is not None:
+            self._mask = np.ascontiguousarray(mask, dtype=np.uint8)
+            if self._mask.size != self.N:
+                raise ValueError("mask size != nx*ny*nz")
+            mptr = self._mask.ctypes.data
+        h = C.c_void_p()
+        rc = _lib.lbm_create(C.byref(h), lattice, nx, ny, nz, eos, t_over_tc, kappa, tau,
+                             mptr, C.byref(p))
+        if rc:
+            raise LBMError(rc, "lbm_create rejected the arguments")
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream
+        if stream is not None:
+            self._check(_lib.lbm_set_stream(h, C.c_void_p(stream.cuda_stream)))
+        self._mem = None
+        if torch_memory:
+            nbytes = _lib.lbm_required_bytes(lattice, nx, ny, nz, storage)
+            self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self._mem.data_ptr()
+            off = (-base) % 256
+            self._check(_lib.lbm_bind_device_memory(h, C.c_void_p(base + off), nbytes))
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, rc: int):
+        if rc:
+            msg = _lib.lbm_last_error(self._h).decode() if getattr(self, "_h", None) else ""
+            raise LBMError(rc, msg)
+
+    @staticmethod
+    def _on_device(a) -> int:
+        return 0 if a is None or isinstance(a, np.ndarray) else 1
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.lbm_destroy(h)
+            self._h = None
+        self._mem = None
+
+    def __del__(self):
+        self.close()
+
+    # -- C ABI calls -------------------------------------------------------
+    def init(self, rho0, u0=None):
+        dev = self._on_device(rho0)
+        if not dev:
+            rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+            u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+        self._check(_lib.lbm_init(self._h, _ptr(rho0), None if u0 is None else _ptr(u0), dev))
+
+    def step(self, n: int = 1):
+        self._check(_lib.lbm_step(self._h, int(n)))
+
+    def moments(self, out=None):
+        """(rho, u, U). With ``out=None`` returns host numpy arrays; pass a
+        tuple of three device tensors to fill them on the device."""
+        if out is None:
+            rho, u, U = np.empty(self.N), np.empty(self.D * self.N), np.empty(self.D * self.N)
+            self._check(_lib.lbm_moments(self._h, rho.ctypes.data, u.ctypes.data, U.ctypes.data, 0))
+            return rho, u, U
+        rho, u, U = out
+        self._check(_lib.lbm_moments(self._h, *(None if t is None else _ptr(t) for t in out), 1))
+        return rho, u, U
+
+    def reduce(self):
+        m = C.c_double()
+        j = (C.c_double * 3)()
+        self._check(_lib.lbm_reduce(self._h, C.byref(m), j))
+        return m.value, np.array(j[: self.D])
+
+    def get_populations(self, out=None):
+        if out is None:
+            out = np.empty(self.Q * self.N)
+        self._check(_lib.lbm_get_populations(self._h, _ptr(out), self._on_device(out)))
+        return out
+
+    def set_populations(self, f):
+        dev = self._on_device(f)
+        if not dev:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        self._check(_lib.lbm_set_populations(self._h, _ptr(f), dev))
+
+    def sync(self, timeout_ms: int = -1):
+        self._check(_lib.lbm_sync(self._h, int(timeout_ms)))
+
+    def time_kernels(self, n: int):
+        """Mean (moments, collide) kernel durations in ms over n plain steps."""
+        ms = (C.c_double * 2)()
+        self._check(_lib.lbm_time_kernels(self._h, int(n), ms))
+        return ms[0], ms[1]
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.lbm_launch_count(self._h))
+
+    @staticmethod
+    def required_bytes(lattice, nx, ny, nz, storage=F64) -> int:
+        return int(_lib.lbm_required_bytes(lattice, nx, ny, nz, storage))
