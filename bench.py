@@ -31,6 +31,11 @@ ALG_BYTES_PER_LU = {  # populations read once and written once per lattice updat
     (1, 0): 2 * 27 * 8,
     (0, 0): 2 * 9 * 8,
 }
+# FP64 flops per node executed by the collide kernel (D3Q27), counted from
+# the source: stencils 300, force 15, Phi 9, 1/rho 1, product-form factors
+# 54, products 78, collision 108.
+COLLIDE_FP64_FLOPS_PER_NODE = 565
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (an FMA-chain probe measured 1.19)
 
 
 def parse():
@@ -220,6 +225,10 @@ def main():
     peak, peak_kind = measured_peaks()
     alg = ALG_BYTES_PER_LU[(w.lattice, 0)] * w.nodes
     achieved = alg / (ms_collide * 1e-3) / 1e9
+    tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_collide launch
+    # at 96^3 (402.2 MB), scaled by nodes to this workload.
+    traffic = 402.24e6 * w.nodes / 884736 if w.lattice == 1 else None
 
     # end to end through the C ABI with pinned host buffers
     pin_rho0 = torch.from_numpy(rho0).pin_memory()
@@ -258,10 +267,15 @@ def main():
                    "nodes": w.nodes, "storage": "f64", "eos": "Peng-Robinson" if w.eos == 1 else "vdW",
                    "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (27 * 8 * w.nodes / 1e6),
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_collide",
-                     "peak_source": peak_kind, "alg_bytes_per_launch": alg,
-                     "ms_per_launch": ms_collide, "ms_moments_kernel": ms_macro},
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                     "traffic": traffic, "kernel": "k_collide (FP64)",
+                     "peak_source": "nominal FP64 rate of GB300 (recipe table)",
+                     "flops_per_node": COLLIDE_FP64_FLOPS_PER_NODE,
+                     "ms_per_launch": ms_collide, "ms_moments_kernel": ms_macro,
+                     "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
+                     "hbm_peak_source": peak_kind, "hbm_frac": achieved / peak,
+                     "alg_bytes_per_launch": alg},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS",
                 "h2d_bytes_per_step": 8 * w.nodes / args.steps,
