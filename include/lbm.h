@@ -71,7 +71,8 @@ enum lbm_status {
     LBM_ECUDA = 3,       /* a CUDA call failed; see lbm_last_error */
     LBM_ENONFINITE = 4,  /* a density became non-finite or <= 0 */
     LBM_ETIMEOUT = 5,    /* lbm_sync deadline passed; work still in flight */
-    LBM_ESTATE = 6       /* call not valid in the handle's state */
+    LBM_ESTATE = 6,      /* call not valid in the handle's state */
+    LBM_ETOOBIG = 7      /* size beyond a fixed maximum of the library */
 };
 
 /* Flags of lbm_params.flags. */
@@ -159,6 +160,35 @@ int64_t lbm_launch_count(lbm_handle h);
 int lbm_time_kernels(lbm_handle h, int64_t n, double *ms);
 
 const char *lbm_last_error(lbm_handle h);
+
+/* Largest node count lbm_reduce_noalloc accepts (8192 x 8192 nodes). */
+#define LBM_REDUCE_NOALLOC_MAX_NODES 67108864
+
+/* Mass sum_i f_i and momentum sum_i c_i f_i over the fluid nodes of a
+ * caller-owned population array, computed without allocating anything.
+ * The paper has no counterpart: this is for callers that cannot allocate
+ * device memory (a process whose memory pool is reserved or frozen, or code
+ * that only borrows device pointers from another framework). It does what
+ * lbm_reduce does, but on arrays the caller passes and without a handle.
+ *
+ * lattice, nx, ny, nz: as lbm_create (nz = 1 for D2Q9), each >= 1 and at
+ * most LBM_REDUCE_NOALLOC_MAX_NODES nodes in total, else LBM_ETOOBIG.
+ * f_dev: device double[Q*N], layout of lbm_get_populations. mask_dev:
+ * device uint8_t[N] (1 = solid, skipped) or NULL for all fluid. sums_dev:
+ * device double[4] receiving (mass, jx, jy, jz); jz = 0 for D2Q9. stream: a
+ * cudaStream_t or NULL (legacy default stream); the call is asynchronous on
+ * it.
+ *
+ * Scratch: the per-block partial sums live in a 256 KiB array of static
+ * device memory inside the library, present on every GPU that loads it
+ * until the process exits. The first call on a device looks the array up
+ * on that device (make it before any stream capture). Every call shares
+ * the array and overwrites the partials it reads, so nothing needs
+ * clearing, but calls whose kernels overlap on the GPU race: order them on
+ * one stream. Returns LBM_EINVAL for bad arguments, LBM_ECUDA on a failed
+ * launch. Calls no cudaMalloc, cudaFree or allocating library routine. */
+int lbm_reduce_noalloc(int lattice, int nx, int ny, int nz, const double *f_dev,
+                       const uint8_t *mask_dev, double *sums_dev, void *stream);
 
 void lbm_destroy(lbm_handle h);
 

@@ -1,6 +1,7 @@
 """Build the CUDA library ``_build/liblbm.so`` for sm_103a with nvcc.
 
-One translation unit (C ABI plus kernels), one -gencode, in-tree output.
+Two translation units (the C ABI with its kernels, and the allocation-free
+reduction), one -gencode, in-tree output.
 """
 from __future__ import annotations
 
@@ -15,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
-SOURCES = [os.path.join(CSRC, "lbm_api.cu")]
+SOURCES = [os.path.join(CSRC, "lbm_api.cu"), os.path.join(CSRC, "lbm_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + \
     [os.path.join(INCLUDE, "lbm.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

@@ -20,7 +20,7 @@ EOS_VDW, EOS_PR, EOS_RKS, EOS_CS = 0, 1, 2, 3
 F64, F32 = 0, 1
 FLAG_PHI_OFF = 1
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
-          5: "LBM_ETIMEOUT", 6: "LBM_ESTATE"}
+          5: "LBM_ETIMEOUT", 6: "LBM_ESTATE", 7: "LBM_ETOOBIG"}
 
 
 class lbm_params(C.Structure):
@@ -57,6 +57,7 @@ def _load():
     L.lbm_launch_count.restype = i64
     L.lbm_launch_count.argtypes = [vp]
     L.lbm_time_kernels.argtypes = [vp, i64, dp]
+    L.lbm_reduce_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
     L.lbm_destroy.argtypes = [vp]
@@ -80,6 +81,7 @@ lbm_set_populations = _lib.lbm_set_populations
 lbm_sync = _lib.lbm_sync
 lbm_launch_count = _lib.lbm_launch_count
 lbm_time_kernels = _lib.lbm_time_kernels
+lbm_reduce_noalloc = _lib.lbm_reduce_noalloc
 lbm_last_error = _lib.lbm_last_error
 lbm_destroy = _lib.lbm_destroy
 
