@@ -28,8 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALG_BYTES_PER_LU = {  # populations read once and written once per lattice update
-    (1, 0): 2 * 27 * 8,
-    (0, 0): 2 * 9 * 8,
+    (1, "f64"): 2 * 27 * 8,
+    (0, "f64"): 2 * 9 * 8,
+    (1, "f32"): 2 * 27 * 4,
+    (0, "f32"): 2 * 9 * 4,
 }
 # FP64 flops per node executed by the collide kernel (D3Q27), counted from
 # the source: stencils 300, force 15, Phi 9, 1/rho 1, product-form factors
@@ -45,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d3q27_drop_128^3_pr_tr0.7")
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -178,7 +182,7 @@ def main():
     __graft_entry__.build()
     import numpy as np
     import torch
-    from paper_2112_01975_gb300.lbm import LBM
+    from paper_2112_01975_gb300.lbm import F32, F64, LBM
 
     torch.cuda.set_device(local)
     dist = None
@@ -188,7 +192,9 @@ def main():
 
     stream = torch.cuda.Stream()
     g = LBM(w.lattice, w.nx, w.ny, w.nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
-            stream=stream)
+            stream=stream, storage=F32 if args.storage == "f32" else F64)
+    if args.chunk:
+        g.set_chunk(args.chunk)
     rho0 = w.rho0()
     g.init(rho0)
     g.step(args.warmup)
@@ -223,12 +229,27 @@ def main():
     n_t = max(5, min(50, args.steps // 4))
     ms_macro, ms_collide = g.time_kernels(n_t)
     peak, peak_kind = measured_peaks()
-    alg = ALG_BYTES_PER_LU[(w.lattice, 0)] * w.nodes
+    alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * w.nodes
     achieved = alg / (ms_collide * 1e-3) / 1e9
     tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_collide launch
-    # at 96^3 (402.2 MB), scaled by nodes to this workload.
-    traffic = 402.24e6 * w.nodes / 884736 if w.lattice == 1 else None
+    if args.storage == "f64":
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_collide
+        # launch at 96^3 (402.2 MB), scaled by nodes to this workload.
+        traffic = 402.24e6 * w.nodes / 884736 if w.lattice == 1 else None
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                    "traffic": traffic, "kernel": "k_collide (FP64)",
+                    "peak_source": "nominal FP64 rate of GB300 (recipe table)",
+                    "flops_per_node": COLLIDE_FP64_FLOPS_PER_NODE,
+                    "ms_per_launch": ms_collide, "ms_moments_kernel": ms_macro,
+                    "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
+                    "hbm_peak_source": peak_kind, "hbm_frac": achieved / peak,
+                    "alg_bytes_per_launch": alg}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_step_f32 (fused)", "peak_source": peak_kind + " (hbm_gbs)",
+                    "alg_bytes_per_launch": alg, "ms_per_launch": ms_collide}
 
     # end to end through the C ABI with pinned host buffers
     pin_rho0 = torch.from_numpy(rho0).pin_memory()
@@ -262,20 +283,14 @@ def main():
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": w.name, "lattice": "D3Q27" if w.lattice else "D2Q9",
-                   "nodes": w.nodes, "storage": "f64", "eos": "Peng-Robinson" if w.eos == 1 else "vdW",
-                   "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (27 * 8 * w.nodes / 1e6),
+                   "nodes": w.nodes, "storage": args.storage,
+                   "eos": "Peng-Robinson" if w.eos == 1 else "vdW",
+                   "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (
+                       (27 if w.lattice else 9) * (8 if args.storage == "f64" else 4) * w.nodes / 1e6),
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                     "traffic": traffic, "kernel": "k_collide (FP64)",
-                     "peak_source": "nominal FP64 rate of GB300 (recipe table)",
-                     "flops_per_node": COLLIDE_FP64_FLOPS_PER_NODE,
-                     "ms_per_launch": ms_collide, "ms_moments_kernel": ms_macro,
-                     "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
-                     "hbm_peak_source": peak_kind, "hbm_frac": achieved / peak,
-                     "alg_bytes_per_launch": alg},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS",
                 "h2d_bytes_per_step": 8 * w.nodes / args.steps,

@@ -61,7 +61,10 @@ enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q27 = 1 };
  * (Eq. PREoS), Redlich-Kwong-Soave (Eq. RKSEoS), Carnahan-Starling (Eq. CSEos). */
 enum lbm_eos { LBM_EOS_VDW = 0, LBM_EOS_PR = 1, LBM_EOS_RKS = 2, LBM_EOS_CS = 3 };
 
-/* Population storage. LBM_F64 stores and computes in FP64. */
+/* Population storage. LBM_F64 stores and computes in FP64 (two kernels per
+ * step). LBM_F32 stores populations in FP32 and runs the step as one fused
+ * FP32 kernel; moments, reductions and population I/O are still FP64 on
+ * the host side of the ABI. */
 enum lbm_storage { LBM_F64 = 0, LBM_F32 = 1 };
 
 enum lbm_status {
@@ -155,9 +158,15 @@ int64_t lbm_launch_count(lbm_handle h);
 
 /* Advance n >= 1 steps with plain launches, timing each kernel with CUDA
  * events on the handle's stream. ms[0] receives the mean duration of the
- * moments kernel, ms[1] of the collide-and-stream kernel (milliseconds).
- * Synchronising. */
+ * moments kernel, ms[1] of the collide-and-stream kernel (milliseconds);
+ * with LBM_F32 storage the step is one fused kernel, ms[0] = 0 and ms[1]
+ * is its duration. Synchronising. */
 int lbm_time_kernels(lbm_handle h, int64_t n, double *ms);
+
+/* Planes per CTA along the march axis (z; the 2D y axis for D2Q9) of the
+ * fused FP32 step, >= 1 (default 16 for D3Q27, 64 for D2Q9). A tuning knob:
+ * results do not depend on it. */
+int lbm_set_chunk(lbm_handle h, int chunk);
 
 const char *lbm_last_error(lbm_handle h);
 

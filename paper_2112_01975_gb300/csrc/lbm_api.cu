@@ -11,25 +11,31 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_fused_f32.cuh"
 #include "lbm_kernels.cuh"
 
 using lbmk::Geo;
 using lbmk::Phys;
+using lbmf::GeoF;
+using lbmf::PhysF;
 
 struct lbm_ctx {
     int lattice, D, Q;
     Geo geo;
     Phys phys;
+    GeoF geof;     // FP32 fused step: 3D frame (D2Q9: ny = 1, nz = 2D y extent)
+    PhysF physf;
     int storage, flags;
     double t_over_tc, tau;
     std::vector<uint8_t> mask_host;
+    bool any_solid = false;
     int device;
     cudaStream_t own_stream = nullptr, stream = nullptr, cap_stream = nullptr;
     // device memory
     void *base = nullptr;
     bool owns_base = false;
     size_t bytes = 0;
-    double *f[2] = {nullptr, nullptr};
+    void *fv[2] = {nullptr, nullptr};   // population buffers (double or float)
     double2 *rp = nullptr;
     double *u = nullptr, *gflux = nullptr, *partial = nullptr, *sums = nullptr;
     uint8_t *mask = nullptr;
@@ -51,12 +57,19 @@ struct Layout {
     size_t f0, f1, rp, u, g, mask, partial, sums, status, total;
 };
 
-Layout layout_for(int D, int Q, size_t N)
+size_t pop_bytes(int storage) { return storage == LBM_F32 ? sizeof(float) : sizeof(double); }
+
+Layout layout_for(int D, int Q, size_t N, int storage)
 {
     Layout L;
     size_t o = 0;
-    L.f0 = o; o = align_up(o + sizeof(double) * Q * N);
-    L.f1 = o; o = align_up(o + sizeof(double) * Q * N);
+    const size_t pb = pop_bytes(storage);
+    // Either buffer, when it is the dead one between steps, also stages host
+    // I/O: (1 + 2D) doubles per node (more than 9 floats on D2Q9).
+    const size_t fb = pb * Q * N > sizeof(double) * (1 + 2 * D) * N ? pb * Q * N
+                                                                   : sizeof(double) * (1 + 2 * D) * N;
+    L.f0 = o; o = align_up(o + fb);
+    L.f1 = o; o = align_up(o + fb);
     L.rp = o; o = align_up(o + sizeof(double2) * N);
     L.u = o; o = align_up(o + sizeof(double) * D * N);
     L.g = o; o = align_up(o + sizeof(double) * D * N);
@@ -133,8 +146,8 @@ dim3 node_grid(const Geo &g)
 
 int ensure_memory(lbm_ctx *h)
 {
-    if (h->f[0]) return LBM_OK;
-    Layout L = layout_for(h->D, h->Q, h->geo.N);
+    if (h->fv[0]) return LBM_OK;
+    Layout L = layout_for(h->D, h->Q, h->geo.N, h->storage);
     if (!h->base) {
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, L.total);
@@ -147,8 +160,8 @@ int ensure_memory(lbm_ctx *h)
         h->bytes = L.total;
     }
     char *b = static_cast<char *>(h->base);
-    h->f[0] = reinterpret_cast<double *>(b + L.f0);
-    h->f[1] = reinterpret_cast<double *>(b + L.f1);
+    h->fv[0] = b + L.f0;
+    h->fv[1] = b + L.f1;
     h->rp = reinterpret_cast<double2 *>(b + L.rp);
     h->u = reinterpret_cast<double *>(b + L.u);
     h->gflux = reinterpret_cast<double *>(b + L.g);
@@ -162,27 +175,64 @@ int ensure_memory(lbm_ctx *h)
     return LBM_OK;
 }
 
+bool has_solid(const lbm_ctx *h) { return h->any_solid; }
+
+double *f64(lbm_ctx *h, int k) { return static_cast<double *>(h->fv[k]); }
+float *f32(lbm_ctx *h, int k) { return static_cast<float *>(h->fv[k]); }
+
 template <int LAT>
-int launch_step(lbm_ctx *h, cudaStream_t s)
+dim3 fused_grid(const GeoF &g)
 {
-    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
-    const double *src = h->f[h->cur];
-    double *dst = h->f[h->cur ^ 1];
-    lbmk::k_macro<LAT><<<gr, bl, 0, s>>>(h->geo, h->phys, h->mask, src, h->rp, h->u, h->gflux,
-                                         h->status);
-    lbmk::k_collide<LAT><<<gr, bl, 0, s>>>(h->geo, h->phys, h->mask, src, dst, h->rp, h->u,
-                                           h->gflux);
+    using L = lbmf::LatF<LAT>;
+    return dim3((g.nx + L::TX - 1) / L::TX, (g.ny + L::TY - 1) / L::TY,
+                (g.nz + g.chunk - 1) / g.chunk);
+}
+
+template <int LAT>
+void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
+{
+    using L = lbmf::LatF<LAT>;
+    const dim3 gr = fused_grid<LAT>(h->geof);
+    if (has_solid(h))
+        lbmf::k_step_f32<LAT, true><<<gr, L::TX * L::TY, 0, s>>>(h->geof, h->physf, h->mask, src,
+                                                                dst, h->status);
+    else
+        lbmf::k_step_f32<LAT, false><<<gr, L::TX * L::TY, 0, s>>>(h->geof, h->physf, h->mask, src,
+                                                                 dst, h->status);
+}
+
+// One time step; returns the number of kernels launched (0 on error).
+template <int LAT>
+int launch_step(lbm_ctx *h, cudaStream_t s, int *nk)
+{
+    if (h->storage == LBM_F32) {
+        launch_fused<LAT>(h, s, f32(h, h->cur), f32(h, h->cur ^ 1));
+        *nk = 1;
+    } else {
+        const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+        const double *src = f64(h, h->cur);
+        double *dst = f64(h, h->cur ^ 1);
+        lbmk::k_macro<LAT><<<gr, bl, 0, s>>>(h->geo, h->phys, h->mask, src, h->rp, h->u,
+                                             h->gflux, h->status);
+        lbmk::k_collide<LAT><<<gr, bl, 0, s>>>(h->geo, h->phys, h->mask, src, dst, h->rp, h->u,
+                                               h->gflux);
+        *nk = 2;
+    }
     CU(h, cudaGetLastError());
     h->cur ^= 1;
     return LBM_OK;
 }
 
-int step_plain(lbm_ctx *h, cudaStream_t s)
+int step_plain(lbm_ctx *h, cudaStream_t s, int *nk_out = nullptr)
 {
-    int rc = h->lattice == LBM_D2Q9 ? launch_step<0>(h, s) : launch_step<1>(h, s);
-    if (rc == LBM_OK) h->launches += 2;
+    int nk = 0;
+    int rc = h->lattice == LBM_D2Q9 ? launch_step<0>(h, s, &nk) : launch_step<1>(h, s, &nk);
+    if (rc == LBM_OK) h->launches += nk;
+    if (nk_out) *nk_out = nk;
     return rc;
 }
+
+int kernels_per_step(const lbm_ctx *h) { return h->storage == LBM_F32 ? 1 : 2; }
 
 // Two steps (state buffer 0 -> 1 -> 0) captured once on the library's own
 // stream; replayed on the handle's stream.
@@ -195,7 +245,7 @@ int ensure_graph(lbm_ctx *h)
     const int saved = h->cur;
     int rc = step_plain(h, h->cap_stream);
     if (rc == LBM_OK) rc = step_plain(h, h->cap_stream);
-    h->launches -= 4;  // captured, not launched
+    h->launches -= 2 * kernels_per_step(h);  // captured, not launched
     h->cur = saved;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (rc != LBM_OK) {
@@ -235,8 +285,13 @@ template <int LAT>
 int launch_macro_and_out(lbm_ctx *h, double *rho, double *u, double *U)
 {
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
-    lbmk::k_macro<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->f[h->cur], h->rp,
-                                                 h->u, h->gflux, h->status);
+    if (h->storage == LBM_F32)
+        lbmk::k_macro<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask,
+                                                            f32(h, h->cur), h->rp, h->u,
+                                                            h->gflux, h->status);
+    else
+        lbmk::k_macro<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, f64(h, h->cur),
+                                                     h->rp, h->u, h->gflux, h->status);
     lbmk::k_moments_out<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
                                                        rho, u, U);
     CU(h, cudaGetLastError());
@@ -248,7 +303,12 @@ template <int LAT>
 int launch_init(lbm_ctx *h, const double *rho0, const double *u0)
 {
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
-    lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0, h->f[h->cur]);
+    if (h->storage == LBM_F32)
+        lbmk::k_init<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0,
+                                                           f32(h, h->cur));
+    else
+        lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0,
+                                                    f64(h, h->cur));
     lbmk::k_fill_solid<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
                                                       h->gflux);
     CU(h, cudaGetLastError());
@@ -270,8 +330,12 @@ int launch_fill_solid(lbm_ctx *h)
 template <int LAT>
 int launch_reduce(lbm_ctx *h)
 {
-    lbmk::k_reduce_partial<LAT><<<lbmk::RED_BLOCKS, lbmk::RED_THREADS, 0, h->stream>>>(
-        h->geo, h->mask, h->f[h->cur], h->partial);
+    if (h->storage == LBM_F32)
+        lbmk::k_reduce_partial<LAT, float><<<lbmk::RED_BLOCKS, lbmk::RED_THREADS, 0, h->stream>>>(
+            h->geo, h->mask, f32(h, h->cur), h->partial);
+    else
+        lbmk::k_reduce_partial<LAT><<<lbmk::RED_BLOCKS, lbmk::RED_THREADS, 0, h->stream>>>(
+            h->geo, h->mask, f64(h, h->cur), h->partial);
     lbmk::k_reduce_final<<<1, lbmk::RED_BLOCKS, 0, h->stream>>>(h->partial, h->sums);
     CU(h, cudaGetLastError());
     h->launches += 2;
@@ -301,9 +365,9 @@ int lbm_default_params(int eos, lbm_params *p)
 
 size_t lbm_required_bytes(int lattice, int nx, int ny, int nz, int storage)
 {
-    if (!valid_shape(lattice, nx, ny, nz) || storage != LBM_F64) return 0;
+    if (!valid_shape(lattice, nx, ny, nz) || (storage != LBM_F64 && storage != LBM_F32)) return 0;
     const int D = lattice == LBM_D2Q9 ? 2 : 3, Q = lattice == LBM_D2Q9 ? 9 : 27;
-    return layout_for(D, Q, (size_t)nx * ny * nz).total;
+    return layout_for(D, Q, (size_t)nx * ny * nz, storage).total;
 }
 
 int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, double t_over_tc,
@@ -317,7 +381,7 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     lbm_params prm;
     if (p) prm = *p;
     else lbm_default_params(eos, &prm);
-    if (prm.storage != LBM_F64) return LBM_EINVAL;
+    if (prm.storage != LBM_F64 && prm.storage != LBM_F32) return LBM_EINVAL;
     if (!(prm.a > 0.0) || !(prm.b > 0.0) || !(prm.rho_w > 0.0)) return LBM_EINVAL;
     lbm_ctx *h = new (std::nothrow) lbm_ctx();
     if (!h) return LBM_ENOMEM;
@@ -340,9 +404,46 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     ph.omega = 1.0 / tau;
     ph.phi_pref = (prm.flags & LBM_FLAG_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * ph.omega);
     ph.rho_w = prm.rho_w;
+    // FP32 fused step: D2Q9 runs in the 3D frame with one y row.
+    h->geof.nx = nx;
+    h->geof.ny = lattice == LBM_D2Q9 ? 1 : ny;
+    h->geof.nz = lattice == LBM_D2Q9 ? ny : nz;
+    h->geof.N = h->geo.N;
+    h->geof.chunk = lattice == LBM_D2Q9 ? 64 : 16;
+    PhysF &pf = h->physf;
+    pf.eos = eos;
+    pf.a = (float)ph.a;
+    pf.b = (float)ph.b;
+    pf.RT = (float)ph.RT;
+    pf.aalpha = (float)(ph.a * ph.alpha);
+    pf.kappa = (float)kappa;
+    pf.omega = (float)ph.omega;
+    pf.omw = (float)(1.0 - ph.omega);
+    pf.phi_pref = (float)ph.phi_pref;
+    pf.rho_w = (float)prm.rho_w;
+    {
+        // s psi of the solid density, in the FP32 arithmetic of the step
+        const float r = pf.rho_w;
+        float P;
+        const float rep = r * pf.RT / (1.0f - pf.b * r);
+        switch (eos) {
+        case LBM_EOS_VDW: P = rep - pf.a * r * r; break;
+        case LBM_EOS_PR: P = rep - pf.aalpha * r * r / (1.0f + 2.0f * pf.b * r - pf.b * pf.b * r * r); break;
+        case LBM_EOS_RKS: P = rep - pf.aalpha * r * r / (1.0f + pf.b * r); break;
+        default: {
+            const float e = 0.25f * pf.b * r, om = 1.0f - e;
+            P = r * pf.RT * (1.0f + e + e * e - e * e * e) / (om * om * om) - pf.a * r * r;
+        }
+        }
+        const float d = P - r * (1.0f / 3.0f);
+        pf.spsi_w = d > 0.0f ? std::sqrt(d) : -std::sqrt(-d);
+    }
     h->mask_host.assign(h->geo.N, 0);
     if (solid_mask)
-        for (size_t n = 0; n < h->geo.N; ++n) h->mask_host[n] = solid_mask[n] ? 1 : 0;
+        for (size_t n = 0; n < h->geo.N; ++n) {
+            h->mask_host[n] = solid_mask[n] ? 1 : 0;
+            h->any_solid = h->any_solid || solid_mask[n];
+        }
     if (cudaGetDevice(&h->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -357,9 +458,9 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
 int lbm_bind_device_memory(lbm_handle h, void *dev, size_t bytes)
 {
     if (!h || !dev) return LBM_EINVAL;
-    if (h->f[0]) return fail(h, LBM_ESTATE, "device memory already in use");
+    if (h->fv[0]) return fail(h, LBM_ESTATE, "device memory already in use");
     if (reinterpret_cast<uintptr_t>(dev) % kAlign) return fail(h, LBM_EINVAL, "memory not 256-byte aligned");
-    const size_t need = layout_for(h->D, h->Q, h->geo.N).total;
+    const size_t need = layout_for(h->D, h->Q, h->geo.N, h->storage).total;
     if (bytes < need) return fail(h, LBM_ENOMEM, "bound memory %zu < required %zu", bytes, need);
     h->base = dev;
     h->owns_base = false;
@@ -384,7 +485,7 @@ int lbm_init(lbm_handle h, const double *rho0, const double *u0, int on_device)
     const double *r = rho0, *v = u0;
     if (!on_device) {
         // stage through the second population buffer, dead between steps
-        double *st = h->f[1];
+        double *st = static_cast<double *>(h->fv[1]);
         CU(h, cudaMemcpyAsync(st, rho0, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
         r = st;
         if (u0) {
@@ -416,7 +517,7 @@ int lbm_step(lbm_handle h, int64_t n)
         if ((rc = ensure_graph(h))) return rc;
         for (int64_t k = 0; k < n / 2; ++k) {
             CU(h, cudaGraphLaunch(h->graph, h->stream));
-            h->launches += 4;
+            h->launches += 2 * kernels_per_step(h);
         }
         n %= 2;
     }
@@ -432,7 +533,7 @@ int lbm_moments(lbm_handle h, double *rho, double *u, double *U, int on_device)
     const size_t N = h->geo.N, D = h->D;
     double *dr = rho, *du = u, *dU = U;
     if (!on_device) {
-        double *st = h->f[h->cur ^ 1];  // dead between steps
+        double *st = static_cast<double *>(h->fv[h->cur ^ 1]);  // dead between steps
         dr = rho ? st : nullptr;
         du = u ? st + N : nullptr;
         dU = U ? st + N + D * N : nullptr;
@@ -470,8 +571,23 @@ int lbm_get_populations(lbm_handle h, double *f, int on_device)
     if (rc) return rc;
     if (!f) return LBM_EINVAL;
     const size_t N = h->geo.N, QN = (size_t)h->Q * N;
-    CU(h, cudaMemcpyAsync(f, h->f[h->cur], sizeof(double) * QN,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (h->storage == LBM_F32) {
+        if (on_device) {
+            lbmk::k_convert<float, double><<<1024, 256, 0, h->stream>>>(QN, f32(h, h->cur), f);
+            CU(h, cudaGetLastError());
+            h->launches += 1;
+        } else {
+            std::vector<float> tmp(QN);
+            CU(h, cudaMemcpyAsync(tmp.data(), f32(h, h->cur), sizeof(float) * QN,
+                                  cudaMemcpyDeviceToHost, h->stream));
+            CU(h, cudaStreamSynchronize(h->stream));
+            for (size_t k = 0; k < QN; ++k) f[k] = tmp[k];
+        }
+    } else {
+        CU(h, cudaMemcpyAsync(f, f64(h, h->cur), sizeof(double) * QN,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
     rc = read_status(h);
     if (!on_device)
         for (size_t n = 0; n < N; ++n)
@@ -487,8 +603,23 @@ int lbm_set_populations(lbm_handle h, const double *f, int on_device)
     if (rc) return rc;
     const size_t QN = (size_t)h->Q * h->geo.N;
     h->cur = 0;
-    CU(h, cudaMemcpyAsync(h->f[0], f, sizeof(double) * QN,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    if (h->storage == LBM_F32) {
+        if (on_device) {
+            lbmk::k_convert<double, float><<<1024, 256, 0, h->stream>>>(QN, f, f32(h, 0));
+            CU(h, cudaGetLastError());
+            h->launches += 1;
+        } else {
+            std::vector<float> tmp(QN);
+            for (size_t k = 0; k < QN; ++k) tmp[k] = (float)f[k];
+            CU(h, cudaMemcpyAsync(f32(h, 0), tmp.data(), sizeof(float) * QN,
+                                  cudaMemcpyHostToDevice, h->stream));
+            CU(h, cudaStreamSynchronize(h->stream));
+        }
+    } else {
+        CU(h, cudaMemcpyAsync(f64(h, 0), f, sizeof(double) * QN,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              h->stream));
+    }
     CU(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     rc = h->lattice == LBM_D2Q9 ? launch_fill_solid<0>(h) : launch_fill_solid<1>(h);
     if (rc) return rc;
@@ -537,27 +668,35 @@ int lbm_time_kernels(lbm_handle h, int64_t n, double *ms)
     std::vector<cudaEvent_t> ev(3 * n);
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    const bool fused = h->storage == LBM_F32;
     for (int64_t k = 0; k < n; ++k) {
-        const double *src = h->f[h->cur];
-        double *dst = h->f[h->cur ^ 1];
         CU(h, cudaEventRecord(ev[3 * k], h->stream));
-        if (h->lattice == LBM_D2Q9)
-            lbmk::k_macro<0><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, h->rp, h->u,
-                                                       h->gflux, h->status);
-        else
-            lbmk::k_macro<1><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, h->rp, h->u,
-                                                       h->gflux, h->status);
-        CU(h, cudaEventRecord(ev[3 * k + 1], h->stream));
-        if (h->lattice == LBM_D2Q9)
-            lbmk::k_collide<0><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, dst, h->rp,
-                                                         h->u, h->gflux);
-        else
-            lbmk::k_collide<1><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, dst, h->rp,
-                                                         h->u, h->gflux);
+        if (fused) {
+            CU(h, cudaEventRecord(ev[3 * k + 1], h->stream));
+            if (h->lattice == LBM_D2Q9) launch_fused<0>(h, h->stream, f32(h, h->cur), f32(h, h->cur ^ 1));
+            else launch_fused<1>(h, h->stream, f32(h, h->cur), f32(h, h->cur ^ 1));
+            h->launches += 1;
+        } else {
+            const double *src = f64(h, h->cur);
+            double *dst = f64(h, h->cur ^ 1);
+            if (h->lattice == LBM_D2Q9)
+                lbmk::k_macro<0><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, h->rp,
+                                                           h->u, h->gflux, h->status);
+            else
+                lbmk::k_macro<1><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, h->rp,
+                                                           h->u, h->gflux, h->status);
+            CU(h, cudaEventRecord(ev[3 * k + 1], h->stream));
+            if (h->lattice == LBM_D2Q9)
+                lbmk::k_collide<0><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, dst,
+                                                             h->rp, h->u, h->gflux);
+            else
+                lbmk::k_collide<1><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, src, dst,
+                                                             h->rp, h->u, h->gflux);
+            h->launches += 2;
+        }
         CU(h, cudaEventRecord(ev[3 * k + 2], h->stream));
         CU(h, cudaGetLastError());
         h->cur ^= 1;
-        h->launches += 2;
     }
     CU(h, cudaStreamSynchronize(h->stream));
     double t0 = 0.0, t1 = 0.0;
@@ -572,6 +711,18 @@ int lbm_time_kernels(lbm_handle h, int64_t n, double *ms)
     ms[0] = t0 / n;
     ms[1] = t1 / n;
     return read_status(h);
+}
+
+int lbm_set_chunk(lbm_handle h, int chunk)
+{
+    if (!h) return LBM_EINVAL;
+    if (chunk < 1) return fail(h, LBM_EINVAL, "chunk must be >= 1");
+    if (h->geof.chunk != chunk && h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->geof.chunk = chunk;
+    return LBM_OK;
 }
 
 const char *lbm_last_error(lbm_handle h) { return h ? h->err : "null handle"; }

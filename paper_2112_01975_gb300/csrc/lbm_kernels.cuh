@@ -126,9 +126,11 @@ __device__ __forceinline__ void korteweg_force(const Geo &g, const Phys &p,
 }
 
 // Moments, EOS and pseudo-potential of every fluid node; flags bad densities.
-template <int LAT>
+// Populations are stored as T (double, or float for FP32 storage); the
+// arithmetic here is FP64 either way.
+template <int LAT, typename T = double>
 __global__ void k_macro(Geo g, Phys p, const uint8_t *__restrict__ mask,
-                        const double *__restrict__ f, double2 *__restrict__ rp,
+                        const T *__restrict__ f, double2 *__restrict__ rp,
                         double *__restrict__ u, double *__restrict__ gflux,
                         int *__restrict__ status)
 {
@@ -141,7 +143,7 @@ __global__ void k_macro(Geo g, Phys p, const uint8_t *__restrict__ mask,
     // Row sums along x for each (cy, cz), then the moments from them.
     double fi[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fi[i] = f[(size_t)i * g.N + n];
+    for (int i = 0; i < Q; ++i) fi[i] = (double)f[(size_t)i * g.N + n];
     constexpr int R = Q / 3;
     double row[R], jx = 0.0;
 #pragma unroll
@@ -271,10 +273,10 @@ __global__ void k_moments_out(Geo g, Phys p, const uint8_t *__restrict__ mask,
 
 // Equilibrium populations from (rho0, u0) at fluid nodes, zero at solid nodes;
 // solid nodes' side fields get rho_w and zero velocity.
-template <int LAT>
+template <int LAT, typename T = double>
 __global__ void k_init(Geo g, Phys p, const uint8_t *__restrict__ mask,
                        const double *__restrict__ rho0, const double *__restrict__ u0,
-                       double *__restrict__ f)
+                       T *__restrict__ f)
 {
     constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -283,7 +285,7 @@ __global__ void k_init(Geo g, Phys p, const uint8_t *__restrict__ mask,
     const unsigned n = x + g.nx * (y + g.ny * z);
     if (mask[n]) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[(size_t)i * g.N + n] = 0.0;
+        for (int i = 0; i < Q; ++i) f[(size_t)i * g.N + n] = (T)0;
         return;
     }
     const double rho = rho0[n];
@@ -300,7 +302,7 @@ __global__ void k_init(Geo g, Phys p, const uint8_t *__restrict__ mask,
     for (int i = 0; i < Q; ++i) {
         double eq = rho * E[0][cxi(i) + 1] * E[1][cyi(i) + 1];
         if (D == 3) eq *= E[2][czi(i) + 1];
-        f[(size_t)i * g.N + n] = eq;
+        f[(size_t)i * g.N + n] = (T)eq;
     }
 }
 
@@ -332,9 +334,9 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <int LAT>
+template <int LAT, typename T = double>
 __global__ void __launch_bounds__(RED_THREADS)
-k_reduce_partial(Geo g, const uint8_t *__restrict__ mask, const double *__restrict__ f,
+k_reduce_partial(Geo g, const uint8_t *__restrict__ mask, const T *__restrict__ f,
                  double *__restrict__ partial)
 {
     constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
@@ -344,7 +346,7 @@ k_reduce_partial(Geo g, const uint8_t *__restrict__ mask, const double *__restri
         if (mask[n]) continue;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double fi = f[(size_t)i * g.N + n];
+            const double fi = (double)f[(size_t)i * g.N + n];
             acc[0] += fi;
             if (cxi(i)) acc[1] += cxi(i) * fi;
             if (cyi(i)) acc[2] += cyi(i) * fi;
@@ -387,6 +389,15 @@ k_reduce_final(const double *__restrict__ partial, double *__restrict__ out)
             if (lane == 0) out[k] = v;
         }
     }
+}
+
+// Element-wise type conversion (population I/O of FP32 storage).
+template <typename A, typename B>
+__global__ void k_convert(size_t n, const A *__restrict__ in, B *__restrict__ out)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        out[k] = (B)in[k];
 }
 
 }  // namespace lbmk

@@ -57,6 +57,7 @@ def _load():
     L.lbm_launch_count.restype = i64
     L.lbm_launch_count.argtypes = [vp]
     L.lbm_time_kernels.argtypes = [vp, i64, dp]
+    L.lbm_set_chunk.argtypes = [vp, C.c_int]
     L.lbm_reduce_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
@@ -81,6 +82,7 @@ lbm_set_populations = _lib.lbm_set_populations
 lbm_sync = _lib.lbm_sync
 lbm_launch_count = _lib.lbm_launch_count
 lbm_time_kernels = _lib.lbm_time_kernels
+lbm_set_chunk = _lib.lbm_set_chunk
 lbm_reduce_noalloc = _lib.lbm_reduce_noalloc
 lbm_last_error = _lib.lbm_last_error
 lbm_destroy = _lib.lbm_destroy
@@ -224,6 +226,9 @@ class LBM:
         ms = (C.c_double * 2)()
         self._check(_lib.lbm_time_kernels(self._h, int(n), ms))
         return ms[0], ms[1]
+
+    def set_chunk(self, chunk: int):
+        self._check(_lib.lbm_set_chunk(self._h, int(chunk)))
 
     @property
     def launches(self) -> int:
