@@ -1,11 +1,13 @@
 """Throughput of the two-phase lattice Boltzmann step on GB300.
 
 Workload: D3Q27 static drop, 128^3 periodic, Peng-Robinson EOS at T/Tc = 0.7,
-drop radius 24, FP64 (seeded synthetic init, see paper_2112_01975_gb300/inputs.py).
-One bench step = one lattice time step over all 128^3 nodes (moments, EOS,
-Korteweg force, correction, collision, streaming). Metric: MLUPS (million
-lattice-node updates per second), whole job. The population buffers
-(2 x 453 MB) exceed the 129 MB L2, so no flush is needed between steps.
+drop radius 24 (seeded synthetic init, see paper_2112_01975_gb300/inputs.py),
+FP32 storage with the fused FP32 step by default; the FP64 path is timed on
+the same workload and reported under "f64". One bench step = one lattice
+time step over all 128^3 nodes (moments, EOS, Korteweg force, correction,
+collision, streaming). Metric: MLUPS (million lattice-node updates per
+second), whole job. The population buffers (2 x 226 MB in FP32, 2 x 453 MB in
+FP64) exceed the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -43,13 +45,14 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (an FMA-chain probe measured
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d3q27_drop_128^3_pr_tr0.7")
-    ap.add_argument("--storage", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32"])
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
     return ap.parse_args()
 
 
@@ -169,6 +172,35 @@ def run_reference(args, w, world, rank):
     }), flush=True)
 
 
+def timed_steps(g, stream, steps, dist, local):
+    """Time exactly `steps` lattice steps (graph replays) with CUDA events on
+    the handle's stream, barrier + synchronize on both sides."""
+    import torch
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    l0 = g.launches
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    l1 = g.launches
+    barrier()
+    g.sync()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, l1 - l0
+
+
 def main():
     args = parse()
     from paper_2112_01975_gb300 import inputs
@@ -180,9 +212,9 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    import numpy as np
+    import ctypes
     import torch
-    from paper_2112_01975_gb300.lbm import F32, F64, LBM
+    from paper_2112_01975_gb300.lbm import F32, F64, LBM, _lib
 
     torch.cuda.set_device(local)
     dist = None
@@ -191,39 +223,19 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     stream = torch.cuda.Stream()
+    storage = F32 if args.storage == "f32" else F64
     g = LBM(w.lattice, w.nx, w.ny, w.nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
-            stream=stream, storage=F32 if args.storage == "f32" else F64)
-    if args.chunk:
-        g.set_chunk(args.chunk)
+            stream=stream, storage=storage)
     rho0 = w.rho0()
     g.init(rho0)
+    if storage == F32:
+        chunk = args.chunk or g.autotune()
+        g.set_chunk(chunk)
     g.step(args.warmup)
     g.sync()
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
-        barrier()
-        l0 = g.launches
-        e0.record(stream)
-        g.step(args.steps)
-        e1.record(stream)
-        e1.synchronize()
-        l1 = g.launches
-        barrier()
-    g.sync()
-    ms = e0.elapsed_time(e1)
-    tmax = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-    mlups = w.nodes * args.steps * world / (tmax * 1e-3) / 1e6
+        ms, launches = timed_steps(g, stream, args.steps, dist, local)
+    mlups = w.nodes * args.steps * world / (ms * 1e-3) / 1e6
 
     # per-kernel durations (plain launches with events between kernels)
     n_t = max(5, min(50, args.steps // 4))
@@ -231,45 +243,64 @@ def main():
     peak, peak_kind = measured_peaks()
     alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * w.nodes
     achieved = alg / (ms_collide * 1e-3) / 1e9
-    tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
-    if args.storage == "f64":
-        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_collide
-        # launch at 96^3 (402.2 MB), scaled by nodes to this workload.
-        traffic = 402.24e6 * w.nodes / 884736 if w.lattice == 1 else None
+    if storage == F32:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_step_f32 (fused step)", "peak_source": peak_kind + " hbm_gbs",
+                    "alg_bytes_per_launch": alg, "ms_per_launch": ms_collide,
+                    "chunk": chunk}
+    else:
+        tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                    "traffic": traffic, "kernel": "k_collide (FP64)",
+                    "traffic": 402.24e6 * w.nodes / 884736 if w.lattice == 1 else None,
+                    "kernel": "k_collide (FP64)",
                     "peak_source": "nominal FP64 rate of GB300 (recipe table)",
                     "flops_per_node": COLLIDE_FP64_FLOPS_PER_NODE,
                     "ms_per_launch": ms_collide, "ms_moments_kernel": ms_macro,
-                    "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
-                    "hbm_peak_source": peak_kind, "hbm_frac": achieved / peak,
-                    "alg_bytes_per_launch": alg}
-    else:
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_step_f32 (fused)", "peak_source": peak_kind + " (hbm_gbs)",
-                    "alg_bytes_per_launch": alg, "ms_per_launch": ms_collide}
+                    "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
 
     # end to end through the C ABI with pinned host buffers
+    D = 3 if w.lattice else 2
     pin_rho0 = torch.from_numpy(rho0).pin_memory()
     out_rho = torch.empty(w.nodes, dtype=torch.float64).pin_memory()
-    out_u = torch.empty(3 * w.nodes if w.lattice else 2 * w.nodes, dtype=torch.float64).pin_memory()
-    barrier()
+    out_u = torch.empty(D * w.nodes, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     g.init(pin_rho0.numpy())
     g.step(args.steps)
-    from paper_2112_01975_gb300.lbm import _lib
-    import ctypes
     g._check(_lib.lbm_moments(g._h, ctypes.c_void_p(out_rho.data_ptr()),
                               ctypes.c_void_p(out_u.data_ptr()), None, 0))
     t_e2e = time.perf_counter() - t0
-    barrier()
-    e2e_mlups = w.nodes * args.steps * world / t_e2e / 1e6
     if dist is not None:
         t = torch.tensor([t_e2e], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mlups = w.nodes * args.steps * world / float(t.item()) / 1e6
+        t_e2e = float(t.item())
+    e2e_mlups = w.nodes * args.steps * world / t_e2e / 1e6
+
+    # the FP64 path on the same workload, reported beside the headline
+    f64 = None
+    if storage == F32 and not args.no_f64:
+        g.close()
+        del g
+        h = LBM(w.lattice, w.nx, w.ny, w.nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
+                stream=stream, storage=F64)
+        h.init(rho0)
+        h.step(5)
+        k64 = max(20, args.steps // 10)
+        ms64, _ = timed_steps(h, stream, k64, dist, local)
+        m64, c64 = h.time_kernels(10)
+        f64 = {"value": w.nodes * k64 * world / (ms64 * 1e-3) / 1e6, "unit": "MLUPS",
+               "steps": k64, "ms_per_step": ms64 / k64,
+               "roofline": {"bound": "alu", "kernel": "k_collide (FP64)",
+                            "achieved": COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (c64 * 1e-3) / 1e12,
+                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (c64 * 1e-3) / 1e12
+                            / FP64_PEAK_TFLOPS,
+                            "ms_per_launch": c64, "ms_moments_kernel": m64}}
+        h.close()
 
     if rank != 0:
         if dist is not None:
@@ -282,7 +313,7 @@ def main():
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": w.name, "lattice": "D3Q27" if w.lattice else "D2Q9",
                    "nodes": w.nodes, "storage": args.storage,
@@ -294,9 +325,10 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS",
                 "h2d_bytes_per_step": 8 * w.nodes / args.steps,
-                "d2h_bytes_per_step": 8 * (1 + (3 if w.lattice else 2)) * w.nodes / args.steps},
-        "gpu_launches": l1 - l0,
+                "d2h_bytes_per_step": 8 * (1 + D) * w.nodes / args.steps},
+        "gpu_launches": launches,
         "clocks": clocks.summary(),
+        "f64": f64,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -168,6 +168,13 @@ int lbm_time_kernels(lbm_handle h, int64_t n, double *ms);
  * results do not depend on it. */
 int lbm_set_chunk(lbm_handle h, int chunk);
 
+/* Pick the chunk of the fused FP32 step by timing candidates on the
+ * handle's own state (saved to a temporary device buffer and restored
+ * afterwards, so the state is unchanged). Sets and returns it in
+ * *chunk_out (0 for FP64 storage, which has no tile parameter).
+ * Synchronising; allocates and frees one state-sized buffer. */
+int lbm_autotune(lbm_handle h, int *chunk_out);
+
 const char *lbm_last_error(lbm_handle h);
 
 /* Largest node count lbm_reduce_noalloc accepts (8192 x 8192 nodes). */

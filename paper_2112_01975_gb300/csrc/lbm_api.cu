@@ -422,7 +422,7 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     pf.phi_pref = (float)ph.phi_pref;
     pf.rho_w = (float)prm.rho_w;
     {
-        // s psi of the solid density, in the FP32 arithmetic of the step
+        // P - P0 of the solid density, in FP32
         const float r = pf.rho_w;
         float P;
         const float rep = r * pf.RT / (1.0f - pf.b * r);
@@ -436,7 +436,7 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
         }
         }
         const float d = P - r * (1.0f / 3.0f);
-        pf.spsi_w = d > 0.0f ? std::sqrt(d) : -std::sqrt(-d);
+        pf.spsi_w = d;
     }
     h->mask_host.assign(h->geo.N, 0);
     if (solid_mask)
@@ -711,6 +711,54 @@ int lbm_time_kernels(lbm_handle h, int64_t n, double *ms)
     ms[0] = t0 / n;
     ms[1] = t1 / n;
     return read_status(h);
+}
+
+int lbm_autotune(lbm_handle h, int *chunk_out)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (h->storage != LBM_F32) {
+        if (chunk_out) *chunk_out = 0;
+        return LBM_OK;   // the FP64 step has no tile parameters
+    }
+    if (h->bad) return fail(h, LBM_ESTATE, "state holds a non-finite density; re-initialise");
+    const size_t bytes = sizeof(float) * (size_t)h->Q * h->geo.N;
+    void *save = nullptr;
+    if (cudaMalloc(&save, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LBM_ENOMEM, "autotune: no room to save the state");
+    }
+    CU(h, cudaMemcpyAsync(save, h->fv[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128};
+    const int nz = h->geof.nz;
+    int best = h->geof.chunk;
+    double best_ms = 1e30;
+    for (int c : cands) {
+        if (c > nz && c != cands[0]) continue;
+        h->geof.chunk = c;
+        double ms[2];
+        rc = lbm_time_kernels(h, 1, ms);                  // warm-up
+        if (rc == LBM_OK) rc = lbm_time_kernels(h, 6, ms);
+        if (rc != LBM_OK) break;
+        if (ms[1] < best_ms) { best_ms = ms[1]; best = c; }
+    }
+    cudaError_t e = cudaMemcpyAsync(h->fv[0], save, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(save);
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
+    h->cur = 0;
+    if (rc != LBM_OK) return rc;
+    if (h->graph && h->geof.chunk != best) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->geof.chunk = best;
+    if (h->graph) {   // the captured graph may have been made with another chunk
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (chunk_out) *chunk_out = best;
+    return LBM_OK;
 }
 
 int lbm_set_chunk(lbm_handle h, int chunk)

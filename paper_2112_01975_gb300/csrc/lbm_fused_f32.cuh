@@ -28,7 +28,7 @@ struct PhysF {
     int eos;
     float a, b, RT, aalpha;
     float kappa, omega, omw, phi_pref;  // omw = 1 - omega
-    float rho_w, spsi_w;                // virtual solid density and its s psi
+    float rho_w, spsi_w;                // virtual solid density and its P - P0
 };
 
 // Lattice description in the 3D frame: D2Q9 uses (cx, 0, cy).
@@ -46,27 +46,32 @@ template <> struct LatF<1> {
     __device__ static constexpr int cz(int i) { return i / 9 - 1; }
 };
 
-__device__ __forceinline__ float eos_pressure_f(const PhysF &p, float rho)
+// P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 equations of state).
+__device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
 {
-    const float rep = rho * p.RT / (1.0f - p.b * rho);
+    const float br = p.b * rho, r3 = rho * (1.0f / 3.0f);
     switch (p.eos) {
-    case 0: return rep - p.a * rho * rho;
-    case 1: return rep - p.aalpha * rho * rho / (1.0f + 2.0f * p.b * rho - p.b * p.b * rho * rho);
-    case 2: return rep - p.aalpha * rho * rho / (1.0f + p.b * rho);
+    case 0:
+        return rho * p.RT * __frcp_rn(1.0f - br) - p.a * rho * rho - r3;
+    case 1: {
+        const float d1 = 1.0f - br, d2 = 1.0f + 2.0f * br - br * br;
+        return (rho * p.RT * d2 - p.aalpha * rho * rho * d1) * __frcp_rn(d1 * d2) - r3;
+    }
+    case 2: {
+        const float d1 = 1.0f - br, d2 = 1.0f + br;
+        return (rho * p.RT * d2 - p.aalpha * rho * rho * d1) * __frcp_rn(d1 * d2) - r3;
+    }
     default: {
-        const float e = 0.25f * p.b * rho, om = 1.0f - e;
-        return rho * p.RT * (1.0f + e + e * e - e * e * e) / (om * om * om) - p.a * rho * rho;
+        const float e = 0.25f * br, om = 1.0f - e;
+        return rho * p.RT * (1.0f + e + e * e - e * e * e) * __frcp_rn(om * om * om) -
+               p.a * rho * rho - r3;
     }
     }
-}
-
-__device__ __forceinline__ float signed_psi_f(const PhysF &p, float rho)
-{
-    const float d = eos_pressure_f(p, rho) - rho * (1.0f / 3.0f);
-    return d > 0.0f ? sqrtf(d) : -sqrtf(-d);
 }
 
 __device__ __forceinline__ int wrapf(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 template <int LAT, bool MASK>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
@@ -77,12 +82,13 @@ k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__res
     constexpr int Q = L::Q, TX = L::TX, TY = L::TY, HY = L::HY;
     constexpr bool THREE = LAT == 1;
     constexpr int NT = TX * TY;
-    constexpr int AX = TX + 4, AY = TY + 2 * HY;          // (rho, s psi) halo tile
+    constexpr int AX = TX + 4, AY = TY + 2 * HY;          // (rho, |psi|) halo tile
     constexpr int GX = TX + 2, GY = THREE ? TY + 2 : 1;   // rho u^3 halo tile
     constexpr int RS = 6, GS = 5;                          // ring slots
-    __shared__ float2 s_rp[RS][AY][AX];
+    __shared__ float2 s_rp[RS][AY][AX];                    // (rho, |psi|)
+    __shared__ float s_sg[RS][TY][TX];                     // sign of P - P0, interior
     __shared__ float s_g[GS][3][GY][GX];
-    __shared__ int s_xw[AX], s_yw[AY];   // wrapped halo coordinates (any size >= 5)
+    __shared__ int s_xw[AX], s_yw[AY];                     // wrapped halo coordinates
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -91,63 +97,90 @@ k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__res
     const int tx = tid % TX, ty = tid / TX;
     const int xi = x0 + tx, yi = y0 + ty;
     const bool inside = xi < g.nx && yi < g.ny;
-    const size_t N = g.N;
+    const unsigned N = g.N;
+    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
     for (int c = tid; c < AX; c += NT) s_xw[c] = ((x0 - 2 + c) % g.nx + g.nx) % g.nx;
     for (int r = tid; r < AY; r += NT) s_yw[r] = THREE ? ((y0 - HY + r) % g.ny + g.ny) % g.ny : 0;
     __syncthreads();
 
     // Planes z0-2 .. z1+1 enter the rings one per iteration; plane z0-2+pl
-    // has ring index pl. Six (rho, s psi) slots and five rho u^3 slots let
+    // has ring index pl. Six (rho, |psi|) slots and five rho u^3 slots let
     // the next plane enter while slower warps still collide: one barrier
     // per plane.
     const int np = (z1 - z0) + 4;
     for (int pl = 0; pl < np; ++pl) {
         // ---- phase A: plane z0 - 2 + pl enters the rings -------------------
+        // Each thread owns up to KA halo nodes and issues all their loads
+        // before any arithmetic, for memory-level parallelism.
         {
+            constexpr int KA = (AX * AY + NT - 1) / NT;
             const int zl = wrapf(z0 - 2 + pl, g.nz);
             const int rs = pl % RS, gs = pl % GS;
-            for (int k = tid; k < AX * AY; k += NT) {
+            float fi[KA][Q];
+            unsigned nk[KA];
+            bool live[KA], solid[KA];
+#pragma unroll
+            for (int u = 0; u < KA; ++u) {
+                const int k = tid + u * NT;
+                live[u] = k < AX * AY;
+                const int kk = live[u] ? k : 0;
+                const int r = kk / AX, c = kk - r * AX;
+                nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
+                solid[u] = MASK && live[u] && mask[nk[u]];
+                if (live[u] && !solid[u]) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) fi[u][i] = __ldg(f + (i * N + nk[u]));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KA; ++u) {
+                if (!live[u]) continue;
+                const int k = tid + u * NT;
                 const int r = k / AX, c = k - r * AX;
-                const int x = s_xw[c];
-                const int y = s_yw[r];
-                const unsigned n = x + g.nx * (y + g.ny * zl);
                 const bool ring1 = c >= 1 && c < AX - 1 && (!THREE || (r >= 1 && r < AY - 1));
-                float rho, sp, gx = 0.0f, gy = 0.0f, gz = 0.0f;
-                if (MASK && mask[n]) {
+                float rho, d, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+                if (solid[u]) {
                     rho = p.rho_w;
-                    sp = p.spsi_w;
+                    d = p.spsi_w;
                 } else {
-                    float fi[Q];
+                    // x-row sums for each (cy, cz), then the moments from them
+                    constexpr int R = Q / 3;
+                    float row[R], jx = 0.0f;
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) fi[i] = __ldg(f + i * N + n);
-                    float sx[3] = {0.0f, 0.0f, 0.0f};   // sums over cx = -1, 0, +1
-                    float jy = 0.0f, jz = 0.0f;
+                    for (int q = 0; q < R; ++q) {
+                        row[q] = fi[u][3 * q] + fi[u][3 * q + 1] + fi[u][3 * q + 2];
+                        jx += fi[u][3 * q + 2] - fi[u][3 * q];
+                    }
+                    rho = 0.0f;
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) sx[L::cx(i) + 1] += fi[i];
-                    rho = sx[0] + sx[1] + sx[2];
+                    for (int q = 0; q < R; ++q) rho += row[q];
                     if (ring1) {
+                        float jy = 0.0f, jz = 0.0f;
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) {
-                            if (L::cy(i) > 0) jy += fi[i];
-                            if (L::cy(i) < 0) jy -= fi[i];
-                            if (L::cz(i) > 0) jz += fi[i];
-                            if (L::cz(i) < 0) jz -= fi[i];
+                        for (int q = 0; q < R; ++q) {
+                            const int cy = THREE ? q % 3 - 1 : 0, cz = THREE ? q / 3 - 1 : q - 1;
+                            if (cy > 0) jy += row[q];
+                            if (cy < 0) jy -= row[q];
+                            if (cz > 0) jz += row[q];
+                            if (cz < 0) jz -= row[q];
                         }
-                        const float inv = 1.0f / rho;
-                        const float ux = (sx[2] - sx[0]) * inv, uy = jy * inv, uz = jz * inv;
+                        const float inv = __frcp_rn(rho);
+                        const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
                         gx = rho * ux * ux * ux;
                         gy = rho * uy * uy * uy;
                         gz = rho * uz * uz * uz;
                     }
-                    sp = signed_psi_f(p, rho);
+                    d = excess_pressure_f(p, rho);
                 }
-                s_rp[rs][r][c] = make_float2(rho, sp);
+                s_rp[rs][r][c] = f2(rho, sqrtf(fabsf(d)));
                 if (ring1) {
                     const int gr = THREE ? r - 1 : 0;
                     s_g[gs][0][gr][c - 1] = gx;
                     s_g[gs][1][gr][c - 1] = gy;
                     s_g[gs][2][gr][c - 1] = gz;
                 }
+                const int ir = r - HY, ic = c - 2;
+                if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
             }
         }
         __syncthreads();
@@ -155,56 +188,71 @@ k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__res
         if (pl >= 4 && inside) {
             const int pc = pl - 2;             // ring index of the collided plane
             const int zc = z0 + pl - 4;
-            const unsigned n = xi + g.nx * (yi + g.ny * zc);
+            const unsigned n = (unsigned)xi + (unsigned)g.nx * (unsigned)yi + plane * (unsigned)zc;
             if (!(MASK && mask[n])) {
+                // the node's own populations (second read, an L2 hit), issued first
+                float fi[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) fi[i] = __ldg(f + (i * N + n));
                 const int cr = ty + HY, cc = tx + 2;
                 const float2 c0 = s_rp[pc % RS][cr][cc];
                 const float rho = c0.x;
+                const float spsi = s_sg[pc % RS][ty][tx] * c0.y;
                 if (!(rho > 0.0f) || !isfinite(rho)) atomicOr(status, 1);
-                // Korteweg force (Eq. Kforce_final, sign as the force on the fluid)
-                float Sp[3] = {0.0f, 0.0f, 0.0f}, Sr[3] = {0.0f, 0.0f, 0.0f};
+                // Korteweg force (Eq. Kforce_final, sign as the force on the fluid).
+                // Per ring s, the pairs (|psi|, rho) of neighbours with c_a = +1 and
+                // c_a = -1 are summed by weight class (centre, edge, corner).
+                int slot[5];
+#pragma unroll
+                for (int dz = 0; dz < 5; ++dz) slot[dz] = (pc - 2 + dz) % RS;
+                float2 S[3] = {f2(0.0f, 0.0f), f2(0.0f, 0.0f), f2(0.0f, 0.0f)};   // (S_psi, S_rho)
+                const float2 neg1 = f2(-1.0f, -1.0f);
 #pragma unroll
                 for (int s = 1; s <= 2; ++s) {
-                    float ap[3][3], ar[3][3];
+                    float2 P[3][3], M[3][3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) { ap[a][k] = 0.0f; ar[a][k] = 0.0f; }
+                        for (int k = 0; k < 3; ++k) { P[a][k] = f2(0.0f, 0.0f); M[a][k] = f2(0.0f, 0.0f); }
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
                         const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
                         if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
-                        const float2 v = s_rp[(pc + s * c[2] + RS) % RS][cr + s * c[1]][cc + s * c[0]];
-                        const float ps = fabsf(v.y);
+                        const float2 r2 = s_rp[slot[2 + s * c[2]]][cr + s * c[1]][cc + s * c[0]];
+                        const float2 v = f2(r2.y, r2.x);   // (|psi|, rho)
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             if (c[a] == 0) continue;
                             const int k = (a != 0 && c[0] != 0) + (a != 1 && c[1] != 0) +
                                           (a != 2 && c[2] != 0);
-                            if (c[a] > 0) { ap[a][k] += ps; ar[a][k] += v.x; }
-                            else          { ap[a][k] -= ps; ar[a][k] -= v.x; }
+                            if (c[a] > 0) P[a][k] = __fadd2_rn(P[a][k], v);
+                            else          M[a][k] = __fadd2_rn(M[a][k], v);
                         }
                     }
-                    const float gp = s == 1 ? 4.0f / 3.0f : -1.0f / 6.0f;
-                    const float gr = s == 1 ? 2.0f : -1.0f;
+                    // weights w_i/cs2 c_a = 1/2 W(c_b) W(c_c): D3Q27 2/9, 1/18, 1/72;
+                    // D2Q9 1/3, 1/12; ring coefficients (4/3, 2) and (-1/6, -1)
+                    const float2 gsr = s == 1 ? f2(4.0f / 3.0f, 2.0f) : f2(-1.0f / 6.0f, -1.0f);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         if (!THREE && a == 1) continue;
-                        float dp, dr;
+                        const float2 D0 = __ffma2_rn(M[a][0], neg1, P[a][0]);
+                        const float2 D1 = __ffma2_rn(M[a][1], neg1, P[a][1]);
+                        float2 Dw;
                         if (THREE) {
-                            dp = (2.0f / 9.0f) * ap[a][0] + (1.0f / 18.0f) * ap[a][1] + (1.0f / 72.0f) * ap[a][2];
-                            dr = (2.0f / 9.0f) * ar[a][0] + (1.0f / 18.0f) * ar[a][1] + (1.0f / 72.0f) * ar[a][2];
+                            const float2 D2 = __ffma2_rn(M[a][2], neg1, P[a][2]);
+                            Dw = __fmul2_rn(D0, f2(2.0f / 9.0f, 2.0f / 9.0f));
+                            Dw = __ffma2_rn(D1, f2(1.0f / 18.0f, 1.0f / 18.0f), Dw);
+                            Dw = __ffma2_rn(D2, f2(1.0f / 72.0f, 1.0f / 72.0f), Dw);
                         } else {
-                            dp = (1.0f / 3.0f) * ap[a][0] + (1.0f / 12.0f) * ap[a][1];
-                            dr = (1.0f / 3.0f) * ar[a][0] + (1.0f / 12.0f) * ar[a][1];
+                            Dw = __fmul2_rn(D0, f2(1.0f / 3.0f, 1.0f / 3.0f));
+                            Dw = __ffma2_rn(D1, f2(1.0f / 12.0f, 1.0f / 12.0f), Dw);
                         }
-                        Sp[a] += gp * dp;
-                        Sr[a] += gr * dr;
+                        S[a] = __ffma2_rn(Dw, gsr, S[a]);
                     }
                 }
                 float F[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) F[a] = -2.0f * c0.y * Sp[a] - p.kappa * rho * Sr[a];
+                for (int a = 0; a < 3; ++a) F[a] = -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y;
                 // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2
                 const int gr0 = THREE ? ty + 1 : 0, gc0 = tx + 1;
                 float Phi[3];
@@ -214,39 +262,46 @@ k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__res
                                : 0.0f;
                 Phi[2] = p.phi_pref * 0.5f *
                          (s_g[(pc + 1) % GS][2][gr0][gc0] - s_g[(pc - 1) % GS][2][gr0][gc0]);
-                // the node's populations (second read, from L2) and its velocity
-                float fi[Q];
+                // momentum of the node by x-row sums
+                constexpr int R = Q / 3;
+                float row[R], j[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-                for (int i = 0; i < Q; ++i) fi[i] = __ldg(f + i * N + n);
-                float j[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    if (L::cx(i) > 0) j[0] += fi[i];
-                    if (L::cx(i) < 0) j[0] -= fi[i];
-                    if (L::cy(i) > 0) j[1] += fi[i];
-                    if (L::cy(i) < 0) j[1] -= fi[i];
-                    if (L::cz(i) > 0) j[2] += fi[i];
-                    if (L::cz(i) < 0) j[2] -= fi[i];
+                for (int q = 0; q < R; ++q) {
+                    row[q] = fi[3 * q] + fi[3 * q + 1] + fi[3 * q + 2];
+                    j[0] += fi[3 * q + 2] - fi[3 * q];
                 }
-                const float inv = 1.0f / rho;
-                float E[3][3], S[3][3];
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int cy = THREE ? q % 3 - 1 : 0, cz = THREE ? q / 3 - 1 : q - 1;
+                    if (cy > 0) j[1] += row[q];
+                    if (cy < 0) j[1] -= row[q];
+                    if (cz > 0) j[2] += row[q];
+                    if (cz < 0) j[2] -= row[q];
+                }
+                const float inv = __frcp_rn(rho);
+                // product-form factors, paired (equilibrium, extended)
+                float2 ES[3][3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    if (!THREE && a == 1) {   // no y factor on D2Q9
-                        E[1][0] = E[1][1] = E[1][2] = 1.0f;
-                        S[1][0] = S[1][1] = S[1][2] = 1.0f;
+                    if (!THREE && a == 1) {
+                        ES[1][0] = ES[1][1] = ES[1][2] = f2(1.0f, 1.0f);
                         continue;
                     }
                     const float ua = j[a] * inv;
                     const float ze = 1.0f / 3.0f + ua * ua;
-                    E[a][0] = 0.5f * (ze - ua);
-                    E[a][1] = 1.0f - ze;
-                    E[a][2] = 0.5f * (ze + ua);
                     const float xs = ua + F[a] * inv;
                     const float zs = 1.0f / 3.0f + xs * xs + Phi[a] * inv;
-                    S[a][0] = 0.5f * (zs - xs);
-                    S[a][1] = 1.0f - zs;
-                    S[a][2] = 0.5f * (zs + xs);
+                    ES[a][0] = f2(0.5f * (ze - ua), 0.5f * (zs - xs));
+                    ES[a][1] = f2(1.0f - ze, 1.0f - zs);
+                    ES[a][2] = f2(0.5f * (ze + ua), 0.5f * (zs + xs));
+                }
+                float2 A[3][3];
+                const float2 rr = f2(rho, rho);
+#pragma unroll
+                for (int cx = 0; cx < 3; ++cx) {
+                    const float2 rx = __fmul2_rn(rr, ES[0][cx]);
+#pragma unroll
+                    for (int cy = 0; cy < 3; ++cy) A[cx][cy] = __fmul2_rn(rx, ES[1][cy]);
                 }
                 // post = f* + (1 - omega)(f - feq), pushed to r + c_i
                 const int X[3] = {wrapf(xi - 1, g.nx), xi, wrapf(xi + 1, g.nx)};
@@ -255,10 +310,10 @@ k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__res
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-                    const float eq = rho * E[0][cx + 1] * E[1][cy + 1] * E[2][cz + 1];
-                    const float st = rho * S[0][cx + 1] * S[1][cy + 1] * S[2][cz + 1];
-                    const float post = fmaf(p.omw, fi[i] - eq, st);
-                    const unsigned dst = X[cx + 1] + g.nx * (Y[cy + 1] + g.ny * Z[cz + 1]);
+                    const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
+                    const float post = fmaf(p.omw, fi[i] - es.x, es.y);
+                    const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
+                                         plane * (unsigned)Z[cz + 1];
                     if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = post;
                     else                   fout[i * N + dst] = post;
                 }

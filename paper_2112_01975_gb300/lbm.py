@@ -58,6 +58,7 @@ def _load():
     L.lbm_launch_count.argtypes = [vp]
     L.lbm_time_kernels.argtypes = [vp, i64, dp]
     L.lbm_set_chunk.argtypes = [vp, C.c_int]
+    L.lbm_autotune.argtypes = [vp, C.POINTER(C.c_int)]
     L.lbm_reduce_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
@@ -83,6 +84,7 @@ lbm_sync = _lib.lbm_sync
 lbm_launch_count = _lib.lbm_launch_count
 lbm_time_kernels = _lib.lbm_time_kernels
 lbm_set_chunk = _lib.lbm_set_chunk
+lbm_autotune = _lib.lbm_autotune
 lbm_reduce_noalloc = _lib.lbm_reduce_noalloc
 lbm_last_error = _lib.lbm_last_error
 lbm_destroy = _lib.lbm_destroy
@@ -229,6 +231,13 @@ class LBM:
 
     def set_chunk(self, chunk: int):
         self._check(_lib.lbm_set_chunk(self._h, int(chunk)))
+
+    def autotune(self) -> int:
+        """Time the fused step's chunk candidates on the current state (which
+        is restored) and keep the fastest; returns it (0 for FP64)."""
+        c = C.c_int()
+        self._check(_lib.lbm_autotune(self._h, C.byref(c)))
+        return c.value
 
     @property
     def launches(self) -> int:

@@ -194,3 +194,18 @@ def test_f32_coexistence_within_half_percent_of_fp64(lbm):
     r64 = o.moments()[0].reshape(5, nx)[2]
     assert abs(r32[0] / r64[0] - 1) < 5e-3
     assert abs(r32[64] / r64[64] - 1) < 5e-3
+
+
+
+def test_f32_autotune_keeps_the_state(lbm):
+    w = inputs.DROP_D3Q27_128
+    g = lbm.LBM(1, 64, 48, 40, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
+                storage=lbm.F32)
+    g.init(inputs.add_noise(inputs.drop(64, 48, 40, 10.0, w.rho_v, w.rho_l), 1e-4, 6))
+    g.step(4)
+    f0 = g.get_populations()
+    chunk = g.autotune()
+    assert 1 <= chunk <= 128
+    assert np.array_equal(g.get_populations(), f0)
+    g.step(6)
+    g.sync()
