@@ -175,6 +175,34 @@ int lbm_set_chunk(lbm_handle h, int chunk);
  * Synchronising; allocates and frees one state-sized buffer. */
 int lbm_autotune(lbm_handle h, int *chunk_out);
 
+/* ---- Batches: many lattices advanced by one persistent launch ----------
+ * A batch holds count >= 1 distinct, initialised handles with LBM_F32
+ * storage and the same lattice type, of any sizes and parameters. Each
+ * lbm_batch_step launch gives every member one time step (the fused FP32
+ * step over all members' tiles, spread over a persistent grid of two CTAs
+ * per SM); steps after the first replay a CUDA graph of two launches. Each
+ * member's result is bitwise the same as stepping it alone. While the batch
+ * exists the members' work is ordered on the batch's stream (members must
+ * not be stepped, initialised or written individually); lbm_batch_destroy
+ * hands them back, with their state advanced. Host-side arrays (descriptors, work items) are
+ * copied to device memory allocated by lbm_batch_create. */
+typedef struct lbm_batch_ctx *lbm_batch;
+
+int lbm_batch_create(lbm_batch *out, const lbm_handle *members, int count);
+
+/* Advance every member n >= 0 steps; asynchronous. */
+int lbm_batch_step(lbm_batch b, int64_t n);
+
+/* Wait for the batch; LBM_ENONFINITE if a member saw a bad density. After
+ * it returns, and until the next lbm_batch_step, members may be read
+ * (lbm_moments, lbm_reduce, lbm_get_populations). */
+int lbm_batch_sync(lbm_batch b);
+
+/* Launches issued by the batch (one per step). */
+int64_t lbm_batch_launch_count(lbm_batch b);
+
+void lbm_batch_destroy(lbm_batch b);
+
 const char *lbm_last_error(lbm_handle h);
 
 /* Largest node count lbm_reduce_noalloc accepts (8192 x 8192 nodes). */

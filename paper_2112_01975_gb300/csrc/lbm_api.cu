@@ -1,6 +1,7 @@
 // C ABI of the two-phase lattice Boltzmann library (declared in include/lbm.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -658,6 +659,194 @@ int lbm_sync(lbm_handle h, int timeout_ms)
 }
 
 int64_t lbm_launch_count(lbm_handle h) { return h ? h->launches : -1; }
+
+}  // extern "C"
+
+struct lbm_batch_ctx {
+    std::vector<lbm_ctx *> members;
+    std::vector<int> cur0;   // each member's buffer index when the batch was made
+    std::vector<cudaStream_t> prev;   // each member's stream before the batch
+    int lattice = 0;
+    cudaStream_t stream = nullptr;
+    lbmf::MemberF *d_members[2] = {nullptr, nullptr};   // step parity 0 and 1
+    lbmf::WorkItem *d_items = nullptr;
+    int n_items = 0, grid = 0, parity = 0;
+    cudaGraphExec_t graph = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+template <int LAT>
+void launch_batch(lbm_batch_ctx *b, int parity, cudaStream_t s)
+{
+    lbmf::k_step_f32_batch<LAT><<<b->grid, lbmf::LatF<LAT>::TX * lbmf::LatF<LAT>::TY, 0, s>>>(
+        b->d_members[parity], b->d_items, b->n_items);
+}
+
+void batch_launch(lbm_batch_ctx *b, int parity, cudaStream_t s)
+{
+    if (b->lattice == LBM_D2Q9) launch_batch<0>(b, parity, s);
+    else launch_batch<1>(b, parity, s);
+}
+
+void batch_free(lbm_batch_ctx *b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto *m : b->d_members) if (m) cudaFree(m);
+    if (b->d_items) cudaFree(b->d_items);
+    for (size_t k = 0; k < b->prev.size(); ++k) b->members[k]->stream = b->prev[k];
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_batch *out, const lbm_handle *members, int count)
+{
+    if (!out || !members || count < 1) return LBM_EINVAL;
+    *out = nullptr;
+    const int lattice = members[0] ? members[0]->lattice : -1;
+    for (int k = 0; k < count; ++k) {
+        lbm_ctx *h = members[k];
+        if (!h || !h->initialised || h->bad || h->storage != LBM_F32 || h->lattice != lattice)
+            return LBM_EINVAL;
+        for (int j = 0; j < k; ++j)
+            if (members[j] == h) return LBM_EINVAL;   // a lattice at most once
+    }
+    lbm_batch_ctx *b = new (std::nothrow) lbm_batch_ctx();
+    if (!b) return LBM_ENOMEM;
+    b->lattice = lattice;
+    b->members.assign(members, members + count);
+    for (lbm_ctx *h : b->members) {
+        b->cur0.push_back(h->cur);
+        b->prev.push_back(h->stream);
+    }
+    for (lbm_ctx *h : b->members) cudaStreamSynchronize(h->stream);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        batch_free(b);
+        return LBM_ECUDA;
+    }
+    std::vector<lbmf::MemberF> desc[2];
+    std::vector<lbmf::WorkItem> items;
+    for (int k = 0; k < count; ++k) {
+        lbm_ctx *h = b->members[k];
+        const int TX = lattice == LBM_D2Q9 ? lbmf::LatF<0>::TX : lbmf::LatF<1>::TX;
+        const int TY = lattice == LBM_D2Q9 ? lbmf::LatF<0>::TY : lbmf::LatF<1>::TY;
+        const int tx = (h->geof.nx + TX - 1) / TX, ty = (h->geof.ny + TY - 1) / TY;
+        const int tz = (h->geof.nz + h->geof.chunk - 1) / h->geof.chunk;
+        for (int par = 0; par < 2; ++par) {
+            lbmf::MemberF m;
+            m.g = h->geof;
+            m.p = h->physf;
+            m.mask = h->any_solid ? h->mask : nullptr;
+            m.src = static_cast<const float *>(h->fv[h->cur ^ par]);
+            m.dst = static_cast<float *>(h->fv[h->cur ^ par ^ 1]);
+            m.status = h->status;
+            m.tiles_x = tx;
+            m.tiles_y = ty;
+            desc[par].push_back(m);
+        }
+        for (int bz = 0; bz < tz; ++bz)
+            for (int by = 0; by < ty; ++by)
+                for (int bx = 0; bx < tx; ++bx) items.push_back({k, bx, by, bz});
+        h->stream = b->stream;   // members' later work is ordered after the batch
+    }
+    b->n_items = (int)items.size();
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::min(b->n_items, 2 * std::max(sms, 1));
+    const size_t db = sizeof(lbmf::MemberF) * count, ib = sizeof(lbmf::WorkItem) * items.size();
+    if (cudaMalloc(&b->d_members[0], db) != cudaSuccess || cudaMalloc(&b->d_members[1], db) != cudaSuccess ||
+        cudaMalloc(&b->d_items, ib) != cudaSuccess) {
+        batch_free(b);
+        return LBM_ENOMEM;
+    }
+    if (cudaMemcpy(b->d_members[0], desc[0].data(), db, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_members[1], desc[1].data(), db, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_items, items.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess) {
+        batch_free(b);
+        return LBM_ECUDA;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int64_t n)
+{
+    if (!b || n < 0) return LBM_EINVAL;
+    for (lbm_ctx *h : b->members)
+        if (h->bad) return LBM_ESTATE;
+    if (n >= 4) {
+        if (b->parity != 0) {
+            batch_launch(b, b->parity, b->stream);
+            b->parity ^= 1;
+            ++b->launches;
+            --n;
+        }
+        if (!b->graph) {
+            cudaStream_t cap = nullptr;
+            if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
+            cudaGraph_t gr = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                batch_launch(b, 0, cap);
+                batch_launch(b, 1, cap);
+                e = cudaStreamEndCapture(cap, &gr);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) {
+                b->graph = nullptr;
+                cudaGetLastError();
+                return LBM_ECUDA;
+            }
+        }
+        for (int64_t k = 0; k < n / 2; ++k)
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return LBM_ECUDA;
+        b->launches += 2 * (n / 2);
+        n %= 2;
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        batch_launch(b, b->parity, b->stream);
+        b->parity ^= 1;
+        ++b->launches;
+    }
+    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch b)
+{
+    if (!b) return LBM_EINVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBM_ECUDA;
+    // members' state buffers follow the batch parity; their moments, reductions
+    // and population reads are valid between lbm_batch_sync and the next step
+    int bad = LBM_OK;
+    for (size_t k = 0; k < b->members.size(); ++k) {
+        lbm_ctx *h = b->members[k];
+        h->cur = b->cur0[k] ^ b->parity;
+        int rc = read_status(h);
+        if (rc && !bad) bad = rc;
+    }
+    return bad;
+}
+
+int64_t lbm_batch_launch_count(lbm_batch b) { return b ? b->launches : -1; }
+
+void lbm_batch_destroy(lbm_batch b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    for (size_t k = 0; k < b->members.size(); ++k) b->members[k]->cur = b->cur0[k] ^ b->parity;
+    batch_free(b);
+}
 
 int lbm_time_kernels(lbm_handle h, int64_t n, double *ms)
 {

@@ -73,26 +73,42 @@ __device__ __forceinline__ int wrapf(int v, int n) { return v < 0 ? v + n : (v >
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Shared-memory rings of one CTA (static size per lattice type).
+template <int LAT> struct SharedF {
+    using L = LatF<LAT>;
+    static constexpr int TX = L::TX, TY = L::TY, HY = L::HY;
+    static constexpr int AX = TX + 4, AY = TY + 2 * HY;               // (rho, |psi|) halo tile
+    static constexpr int GX = TX + 2, GY = LAT == 1 ? TY + 2 : 1;     // rho u^3 halo tile
+    static constexpr int RS = 6, GS = 5;                               // ring slots
+    float2 rp[RS][AY][AX];   // (rho, |psi|)
+    float sg[RS][TY][TX];    // sign of P - P0, interior nodes
+    float g[GS][3][GY][GX];  // rho u_a^3
+    int xw[AX], yw[AY];      // wrapped halo coordinates
+};
+
+// One CTA's work: the column tile (bx, by) over the plane chunk bz.
 template <int LAT, bool MASK>
-__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
-k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
-           float *__restrict__ fout, int *__restrict__ status)
+__device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
+                                           const uint8_t *__restrict__ mask,
+                                           const float *__restrict__ f, float *__restrict__ fout,
+                                           int *__restrict__ status, int bx, int by, int bz,
+                                           SharedF<LAT> &sm)
 {
     using L = LatF<LAT>;
     constexpr int Q = L::Q, TX = L::TX, TY = L::TY, HY = L::HY;
     constexpr bool THREE = LAT == 1;
     constexpr int NT = TX * TY;
-    constexpr int AX = TX + 4, AY = TY + 2 * HY;          // (rho, |psi|) halo tile
-    constexpr int GX = TX + 2, GY = THREE ? TY + 2 : 1;   // rho u^3 halo tile
-    constexpr int RS = 6, GS = 5;                          // ring slots
-    __shared__ float2 s_rp[RS][AY][AX];                    // (rho, |psi|)
-    __shared__ float s_sg[RS][TY][TX];                     // sign of P - P0, interior
-    __shared__ float s_g[GS][3][GY][GX];
-    __shared__ int s_xw[AX], s_yw[AY];                     // wrapped halo coordinates
+    constexpr int AX = SharedF<LAT>::AX, AY = SharedF<LAT>::AY;
+    constexpr int RS = SharedF<LAT>::RS, GS = SharedF<LAT>::GS;
+    auto &s_rp = sm.rp;
+    auto &s_sg = sm.sg;
+    auto &s_g = sm.g;
+    auto &s_xw = sm.xw;
+    auto &s_yw = sm.yw;
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * g.chunk;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * g.chunk;
     const int z1 = min(z0 + g.chunk, g.nz);
     const int tx = tid % TX, ty = tid / TX;
     const int xi = x0 + tx, yi = y0 + ty;
@@ -319,6 +335,50 @@ k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__res
                 }
             }
         }
+    }
+}
+
+template <int LAT, bool MASK>
+__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
+k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
+           float *__restrict__ fout, int *__restrict__ status)
+{
+    __shared__ SharedF<LAT> sm;
+    fused_tile<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+}
+
+// Many lattices of one type in one launch: descriptor of one member for the
+// current step parity, and the (member, tile) work items.
+struct MemberF {
+    GeoF g;
+    PhysF p;
+    const uint8_t *mask;   // nullptr when the member has no solid node
+    const float *src;
+    float *dst;
+    int *status;
+    int tiles_x, tiles_y;
+};
+
+struct WorkItem {
+    int member, bx, by, bz;
+};
+
+// Persistent: CTA b takes items b, b + gridDim.x, ... (a fixed assignment,
+// so each member's result does not depend on what else is in the batch).
+template <int LAT>
+__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
+k_step_f32_batch(const MemberF *__restrict__ members, const WorkItem *__restrict__ items,
+                 int n_items)
+{
+    __shared__ SharedF<LAT> sm;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const MemberF &m = members[w.member];
+        if (m.mask)
+            fused_tile<LAT, true>(m.g, m.p, m.mask, m.src, m.dst, m.status, w.bx, w.by, w.bz, sm);
+        else
+            fused_tile<LAT, false>(m.g, m.p, m.mask, m.src, m.dst, m.status, w.bx, w.by, w.bz, sm);
+        __syncthreads();   // the rings are reused by the next item
     }
 }
 

@@ -60,6 +60,13 @@ def _load():
     L.lbm_set_chunk.argtypes = [vp, C.c_int]
     L.lbm_autotune.argtypes = [vp, C.POINTER(C.c_int)]
     L.lbm_reduce_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
+    L.lbm_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
+    L.lbm_batch_step.argtypes = [vp, i64]
+    L.lbm_batch_sync.argtypes = [vp]
+    L.lbm_batch_launch_count.restype = i64
+    L.lbm_batch_launch_count.argtypes = [vp]
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
     L.lbm_destroy.argtypes = [vp]
@@ -86,6 +93,11 @@ lbm_time_kernels = _lib.lbm_time_kernels
 lbm_set_chunk = _lib.lbm_set_chunk
 lbm_autotune = _lib.lbm_autotune
 lbm_reduce_noalloc = _lib.lbm_reduce_noalloc
+lbm_batch_create = _lib.lbm_batch_create
+lbm_batch_step = _lib.lbm_batch_step
+lbm_batch_sync = _lib.lbm_batch_sync
+lbm_batch_launch_count = _lib.lbm_batch_launch_count
+lbm_batch_destroy = _lib.lbm_batch_destroy
 lbm_last_error = _lib.lbm_last_error
 lbm_destroy = _lib.lbm_destroy
 
@@ -246,3 +258,39 @@ class LBM:
     @staticmethod
     def required_bytes(lattice, nx, ny, nz, storage=F64) -> int:
         return int(_lib.lbm_required_bytes(lattice, nx, ny, nz, storage))
+
+
+class Batch:
+    """Several FP32 lattices of one type advanced together (lbm_batch_*)."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        h = C.c_void_p()
+        rc = _lib.lbm_batch_create(C.byref(h), arr, len(self.members))
+        if rc:
+            raise LBMError(rc, "lbm_batch_create rejected the members")
+        self._h = h
+
+    def step(self, n: int = 1):
+        rc = _lib.lbm_batch_step(self._h, int(n))
+        if rc:
+            raise LBMError(rc, "lbm_batch_step failed")
+
+    def sync(self):
+        rc = _lib.lbm_batch_sync(self._h)
+        if rc:
+            raise LBMError(rc, "lbm_batch_sync")
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.lbm_batch_launch_count(self._h))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.lbm_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,100 @@
+"""Batches: many FP32 lattices of different sizes and parameters advanced by
+one persistent launch per step. Each member must come out bitwise equal to
+the same lattice stepped alone (the per-tile arithmetic is the same code and
+no data crosses members)."""
+import numpy as np
+import pytest
+
+from paper_2112_01975_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_01975_gb300 import build
+    build.build()
+    from paper_2112_01975_gb300 import lbm as L
+    return L
+
+
+def d3q27_members(L):
+    pr, vdw = inputs.DROP_D3Q27_128, inputs.DROP_D2Q9_64
+    specs = [
+        (40, 36, 33, pr.eos, 0.7, pr.kappa, 1.0, pr.a, pr.rho_v, pr.rho_l, None),
+        (64, 24, 20, vdw.eos, 0.8, vdw.kappa, 0.8, vdw.a, vdw.rho_v, vdw.rho_l,
+         inputs.block_mask(64, 24, 20, (50, 0, 0), (56, 5, 20))),
+        (32, 32, 32, pr.eos, 0.7, pr.kappa, 0.7, pr.a, pr.rho_v, pr.rho_l, None),
+    ]
+    out = []
+    for k, (nx, ny, nz, eos, tr, kap, tau, a, rv, rl, mask) in enumerate(specs):
+        rho = inputs.add_noise(inputs.drop(nx, ny, nz, min(nx, ny, nz) / 4, rv, rl), 1e-4, 30 + k)
+        out.append(((1, nx, ny, nz, eos, tr, kap, tau), dict(a=a, b=2 / 21, mask=mask, rho_w=rv), rho))
+    return out
+
+
+def make(L, spec):
+    args, kw, rho = spec
+    g = L.LBM(*args, storage=L.F32, **kw)
+    g.init(rho)
+    return g
+
+
+@pytest.mark.parametrize("steps", [1, 2, 23])
+def test_batch_equals_alone_d3q27(lbm, steps):
+    specs = d3q27_members(lbm)
+    alone = []
+    for sp in specs:
+        g = make(lbm, sp)
+        g.step(steps)
+        alone.append(g.get_populations())
+    members = [make(lbm, sp) for sp in specs]
+    b = lbm.Batch(members)
+    b.step(steps)
+    b.sync()
+    assert b.launches == steps
+    for g, ref in zip(members, alone):
+        assert np.array_equal(g.get_populations(), ref)
+    b.close()
+
+
+def test_batch_equals_alone_d2q9_and_reads_between_steps(lbm):
+    w = inputs.DROP_D2Q9_64
+    specs = []
+    for k, (nx, ny) in enumerate([(64, 64), (96, 40), (37, 29)]):
+        rho = inputs.add_noise(inputs.drop(nx, ny, 1, min(nx, ny) / 4, w.rho_v, w.rho_l), 1e-4, 40 + k)
+        specs.append(((0, nx, ny, 1, w.eos, w.t_over_tc, w.kappa, 0.9), dict(a=w.a, b=w.b), rho))
+    alone = []
+    for sp in specs:
+        g = make(lbm, sp)
+        g.step(7)
+        mid = g.moments()[0]
+        g.step(10)
+        alone.append((mid, g.get_populations()))
+    members = [make(lbm, sp) for sp in specs]
+    b = lbm.Batch(members)
+    b.step(7)
+    b.sync()
+    mids = [g.moments()[0] for g in members]
+    b.step(10)
+    b.close()
+    for g, m, (mid, ref) in zip(members, mids, alone):
+        assert np.array_equal(m, mid)
+        assert np.array_equal(g.get_populations(), ref)
+    members[0].step(3)     # members are usable on their own after the batch
+    members[0].sync()
+
+
+def test_batch_rejects_mixed_members(lbm):
+    w = inputs.DROP_D2Q9_64
+    a = lbm.LBM(0, 32, 32, 1, w.eos, w.t_over_tc, w.kappa, 1.0, a=w.a, b=w.b, storage=lbm.F32)
+    c = lbm.LBM(0, 32, 32, 1, w.eos, w.t_over_tc, w.kappa, 1.0, a=w.a, b=w.b, storage=lbm.F64)
+    a.init(np.full(1024, 2.0))
+    c.init(np.full(1024, 2.0))
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([a, c])          # FP64 member
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([a, a])          # the same lattice twice
