@@ -1,0 +1,227 @@
+"""Continuous-batching server for parameter-sweep solves.
+
+Requests (a drop on D2Q9 or D3Q27 at some size, T/Tc and radius, a number
+of steps) arrive over time. The server keeps every admitted lattice resident
+on the GPU, admits waiting requests in arrival order as soon as their
+device-memory footprint fits the budget, and advances all resident lattices
+of a lattice type together with one batched launch per step (lbm_batch_*),
+in ticks of a fixed number of steps. A lattice that has finished its steps
+is read back and freed at the end of its tick, which frees room for the
+next arrivals. Every step of every solve runs in the library's kernels; a
+member of a batch evolves bitwise as it would alone.
+
+The one-at-a-time FP64 baseline solves the same requests in arrival order,
+each alone on the GPU with FP64 storage.
+"""
+from __future__ import annotations
+
+import dataclasses
+import hashlib
+import math
+import time
+
+import numpy as np
+
+from . import eos_tables, inputs
+from .lbm import D2Q9, D3Q27, F32, F64, LBM, Batch, LBMError
+
+
+@dataclasses.dataclass(frozen=True)
+class Request:
+    rid: int
+    arrival: float        # seconds after the start of the sweep
+    lattice: int          # 0 = D2Q9, 1 = D3Q27
+    n: int                # side of the square/cubic periodic box
+    t_over_tc: float
+    radius_frac: float    # drop radius / n
+    oscillating: bool     # n = 2 shape mode instead of a round drop
+    steps: int
+    seed: int
+
+    @property
+    def nodes(self) -> int:
+        return self.n ** (3 if self.lattice == D3Q27 else 2)
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    done: float
+    latency: float
+    rho_min: float
+    rho_max: float
+    mass: float
+    digest: str           # sha1 of the final populations ("" unless asked for)
+    failed: bool = False  # a density became non-finite; the solve was dropped
+
+
+def sweep_requests(count: int = 512, rate: float = 50.0, seed: int = 5, steps: int = 5000,
+                   sizes_2d=tuple(range(64, 513, 32)), sizes_3d=tuple(range(64, 193, 32)),
+                   tr=(0.5, 0.95), radius=(0.15, 0.35)) -> list[Request]:
+    """Poisson arrivals (exponential gaps of mean 1/rate); each request a
+    D2Q9 or D3Q27 drop with probability 1/2, size uniform over the given
+    sides, T/Tc and radius fraction uniform in their ranges, round or n = 2
+    oscillating with probability 1/2. All draws from splitmix64(seed ^ k)."""
+    u = (inputs.uniform_pm1(seed, 6 * count) + 1.0) / 2.0   # U[0, 1)
+    u = u.reshape(count, 6)
+    reqs, t = [], 0.0
+    for k in range(count):
+        t += -math.log(1.0 - u[k, 0]) / rate
+        lat = D3Q27 if u[k, 1] >= 0.5 else D2Q9
+        sizes = sizes_3d if lat == D3Q27 else sizes_2d
+        n = sizes[min(int(u[k, 2] * len(sizes)), len(sizes) - 1)]
+        reqs.append(Request(k, t, lat, n, tr[0] + (tr[1] - tr[0]) * u[k, 3],
+                            radius[0] + (radius[1] - radius[0]) * u[k, 4], bool(u[k, 5] >= 0.5),
+                            steps, 1000 + k))
+    return reqs
+
+
+def setup(req: Request):
+    """EOS parameters and the initial density of a request (van der Waals,
+    attraction scaled for a liquid dP/drho of 0.1; interface width 5 on D2Q9
+    and 7 on D3Q27, where width-5 drops below T/Tc ~ 0.65 diverge in FP64 as
+    well as in FP32)."""
+    width = 7.0 if req.lattice == D3Q27 else 5.0
+    a = eos_tables.stable_a(0, req.t_over_tc)
+    rv, rl, _ = eos_tables.coexistence(0, req.t_over_tc, a)
+    kappa = eos_tables.kappa_for_width(0, req.t_over_tc, a, width=width)
+    tau = 0.8 if req.oscillating else 1.0
+    n = req.n
+    nz = n if req.lattice == D3Q27 else 1
+    R0 = req.radius_frac * n
+    if req.oscillating:
+        # R(theta) = R0 (1 + eps cos 2 theta - eps^2 / 2), eps = 0.1 (Sec. 4.3 set-up)
+        z, y, x = np.meshgrid(np.arange(nz), np.arange(n), np.arange(n), indexing="ij")
+        dx, dy = x - n // 2, y - n // 2
+        dz = (z - nz // 2) if nz > 1 else 0
+        r = np.sqrt(dx ** 2 + dy ** 2 + dz ** 2)
+        theta = np.arctan2(dy, dx)
+        Rt = R0 * (1.0 + 0.1 * np.cos(2 * theta) - 0.005)
+        rho = inputs.tanh_interface((r - Rt).ravel(), rl, rv, width)
+    else:
+        rho = inputs.drop(n, n, nz, R0, rv, rl, width=width)
+    rho = inputs.add_noise(rho, 1e-4, req.seed)
+    return dict(eos=0, t_over_tc=req.t_over_tc, kappa=kappa, tau=tau, a=a), rho
+
+
+def footprint(req: Request, storage: int = F32) -> int:
+    nz = req.n if req.lattice == D3Q27 else 1
+    return LBM.required_bytes(req.lattice, req.n, req.n, nz, storage)
+
+
+def _failed(req: Request, t0: float) -> Result:
+    done = time.perf_counter() - t0
+    return Result(req.rid, req.arrival, done, done - req.arrival, float("nan"), float("nan"),
+                  float("nan"), "", failed=True)
+
+
+def _finish(req: Request, g: LBM, t0: float, digest: bool = False) -> Result:
+    rho = g.moments()[0]
+    mass, _ = g.reduce()
+    digest = hashlib.sha1(g.get_populations().tobytes()).hexdigest() if digest else ""
+    done = time.perf_counter() - t0
+    return Result(req.rid, req.arrival, done, done - req.arrival, float(rho.min()),
+                  float(rho.max()), mass, digest)
+
+
+def _open(req: Request, storage: int, prepared) -> LBM:
+    prm, rho = prepared[req.rid]
+    nz = req.n if req.lattice == D3Q27 else 1
+    g = LBM(req.lattice, req.n, req.n, nz, prm["eos"], prm["t_over_tc"], prm["kappa"],
+            prm["tau"], a=prm["a"], storage=storage)
+    g.init(rho)
+    return g
+
+
+class Server:
+    """Continuous batching with admission by device-memory footprint."""
+
+    def __init__(self, hbm_budget: int, tick_steps: int = 250, digest: bool = False):
+        self.hbm_budget = hbm_budget
+        self.tick_steps = tick_steps
+        self.digest = digest
+        self.batch_launches = 0
+        self.peak_resident = 0
+
+    def run(self, requests, prepared=None, realtime: bool = True) -> list[Result]:
+        prepared = prepared or {r.rid: setup(r) for r in requests}
+        pending = sorted(requests, key=lambda r: r.arrival)
+        active = []            # [request, handle, steps left]
+        used, results = 0, []
+        t0 = time.perf_counter()
+        while pending or active:
+            now = time.perf_counter() - t0
+            while pending and (pending[0].arrival <= now or not realtime):
+                need = footprint(pending[0])
+                if need > self.hbm_budget:
+                    raise ValueError(f"request {pending[0].rid} needs {need} B > budget")
+                if used + need > self.hbm_budget:
+                    break
+                req = pending.pop(0)
+                active.append([req, _open(req, F32, prepared), req.steps])
+                used += need
+            self.peak_resident = max(self.peak_resident, len(active))
+            if not active:
+                if pending and realtime:
+                    time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+                continue
+            k = min(self.tick_steps, min(a[2] for a in active))
+            batches = []
+            for lat in (D2Q9, D3Q27):
+                members = [a[1] for a in active if a[0].lattice == lat]
+                if members:
+                    b = Batch(members)
+                    b.step(k)          # both lattice types' launches overlap on the GPU
+                    batches.append(b)
+            for b in batches:
+                try:
+                    b.sync()
+                except LBMError:
+                    pass           # the members are checked one by one below
+                self.batch_launches += b.launches
+                b.close()
+            still = []
+            for a in active:
+                a[2] -= k
+                try:
+                    a[1].sync()
+                    ok = True
+                except LBMError:
+                    ok = False     # isolate a diverged solve; the others go on
+                if not ok or a[2] == 0:
+                    results.append(_finish(a[0], a[1], t0, self.digest) if ok else _failed(a[0], t0))
+                    a[1].close()
+                    used -= footprint(a[0])
+                else:
+                    still.append(a)
+            active = still
+        return results
+
+
+def run_sequential_f64(requests, prepared=None, realtime: bool = True) -> list[Result]:
+    """One request at a time, FP64 storage, in arrival order."""
+    prepared = prepared or {r.rid: setup(r) for r in requests}
+    results = []
+    t0 = time.perf_counter()
+    for req in sorted(requests, key=lambda r: r.arrival):
+        if realtime:
+            time.sleep(max(0.0, req.arrival - (time.perf_counter() - t0)))
+        g = _open(req, F64, prepared)
+        g.step(req.steps)
+        try:
+            g.sync()
+            results.append(_finish(req, g, t0))
+        except LBMError:
+            results.append(_failed(req, t0))
+        g.close()
+    return results
+
+
+def summarize(results) -> dict:
+    ok = [r for r in results if not r.failed]
+    lat = np.array([r.latency for r in ok])
+    span = max(r.done for r in results) - min(r.arrival for r in results)
+    return {"solves": len(ok), "failed": len(results) - len(ok), "solves_per_s": len(ok) / span,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "makespan_s": span}
