@@ -176,6 +176,22 @@ def run_reference(args, w, world, rank):
     }), flush=True)
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """Largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job MLUPS: every rank advances its own replica of `nodes` nodes
+    `steps` times; the job takes as long as the slowest rank."""
+    return nodes * steps * world / (max_ms * 1e-3) / 1e6
+
+
 def timed_steps(g, stream, steps, dist, local):
     """Time exactly `steps` lattice steps (graph replays) with CUDA events on
     the handle's stream, barrier + synchronize on both sides."""
@@ -197,11 +213,7 @@ def timed_steps(g, stream, steps, dist, local):
     l1 = g.launches
     barrier()
     g.sync()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
     return ms, l1 - l0
 
 
@@ -271,7 +283,7 @@ def main():
     g.sync()
     with ClockSampler(local) as clocks:
         ms, launches = timed_steps(g, stream, args.steps, dist, local)
-    mlups = w.nodes * args.steps * world / (ms * 1e-3) / 1e6
+    mlups = job_mlups(w.nodes, args.steps, world, ms)
 
     # per-kernel durations (plain launches with events between kernels)
     n_t = max(5, min(50, args.steps // 4))
@@ -309,12 +321,8 @@ def main():
     g.step(args.steps)
     g._check(_lib.lbm_moments(g._h, ctypes.c_void_p(out_rho.data_ptr()),
                               ctypes.c_void_p(out_u.data_ptr()), None, 0))
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_mlups = w.nodes * args.steps * world / t_e2e / 1e6
+    t_e2e = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    e2e_mlups = job_mlups(w.nodes, args.steps, world, t_e2e * 1e3)
 
     # the FP64 path on the same workload, reported beside the headline
     f64 = None
