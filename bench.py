@@ -36,9 +36,10 @@ ALG_BYTES_PER_LU = {  # populations read once and written once per lattice updat
     (0, "f32"): 2 * 9 * 4,
 }
 # FP64 flops per node executed by the collide kernel (D3Q27), counted from
-# the source: stencils 300, force 15, Phi 9, 1/rho 1, product-form factors
-# 54, products 78, collision 108.
-COLLIDE_FP64_FLOPS_PER_NODE = 565
+# the source: two stencil rings 244 (13 neighbour-pair differences of two
+# fields, 54 signed adds, 42 for the weights, per ring), force 15, Phi 9,
+# 1/rho 1, product-form factors 54, partial products 78, collision 81.
+COLLIDE_FP64_FLOPS_PER_NODE = 482
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (an FMA-chain probe measured 1.19)
 
 

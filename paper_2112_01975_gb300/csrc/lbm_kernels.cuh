@@ -38,14 +38,17 @@ __host__ __device__ constexpr int czi(int i) { return i / 9 - 1; }
 // Pressure of the equations of state of Sec. 3.1 (gas constant 1).
 __device__ __forceinline__ double eos_pressure(const Phys &p, double rho)
 {
-    const double rep = rho * p.RT / (1.0 - p.b * rho);
     switch (p.eos) {
     case 0:  // van der Waals
-        return rep - p.a * rho * rho;
-    case 1:  // Peng-Robinson
-        return rep - p.a * p.alpha * rho * rho / (1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho);
-    case 2:  // Redlich-Kwong-Soave
-        return rep - p.a * p.alpha * rho * rho / (1.0 + p.b * rho);
+        return rho * p.RT / (1.0 - p.b * rho) - p.a * rho * rho;
+    case 1: {  // Peng-Robinson, one division
+        const double d1 = 1.0 - p.b * rho, d2 = 1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho;
+        return (rho * p.RT * d2 - p.a * p.alpha * rho * rho * d1) / (d1 * d2);
+    }
+    case 2: {  // Redlich-Kwong-Soave, one division
+        const double d1 = 1.0 - p.b * rho, d2 = 1.0 + p.b * rho;
+        return (rho * p.RT * d2 - p.a * p.alpha * rho * rho * d1) / (d1 * d2);
+    }
     default: {  // Carnahan-Starling
         const double e = 0.25 * p.b * rho;
         const double om = 1.0 - e;
@@ -90,19 +93,22 @@ __device__ __forceinline__ void korteweg_force(const Geo &g, const Phys &p,
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int k = 0; k < 3; ++k) { ap[a][k] = 0.0; ar[a][k] = 0.0; }
+        // each pair (c_i, -c_i) once: differences of the two neighbours, added
+        // with the sign of c_ia to every component where c_ia != 0
 #pragma unroll
-        for (int i = 0; i < Lattice<LAT>::Q; ++i) {
+        for (int i = Lattice<LAT>::Q / 2 + 1; i < Lattice<LAT>::Q; ++i) {
             const int c[3] = {cxi(i), cyi(i), D == 3 ? czi(i) : 0};
-            if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
-            const unsigned nb = X[c[0] + 1] + g.nx * (Y[c[1] + 1] + g.ny * Z[c[2] + 1]);
-            const double2 v = rp[nb];
-            const double ps = fabs(v.y);
+            const unsigned np_ = X[c[0] + 1] + g.nx * (Y[c[1] + 1] + g.ny * Z[c[2] + 1]);
+            const unsigned nm_ = X[1 - c[0]] + g.nx * (Y[1 - c[1]] + g.ny * Z[1 - c[2]]);
+            const double2 vp = rp[np_], vm = rp[nm_];
+            const double dps = fabs(vp.y) - fabs(vm.y);
+            const double drh = vp.x - vm.x;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 if (c[a] == 0) continue;
                 const int k = (a != 0 && c[0] != 0) + (a != 1 && c[1] != 0) + (a != 2 && c[2] != 0);
-                if (c[a] > 0) { ap[a][k] += ps; ar[a][k] += v.x; }
-                else          { ap[a][k] -= ps; ar[a][k] -= v.x; }
+                if (c[a] > 0) { ap[a][k] += dps; ar[a][k] += drh; }
+                else          { ap[a][k] -= dps; ar[a][k] -= drh; }
             }
         }
         const double gp = s == 1 ? 4.0 / 3.0 : -1.0 / 6.0;
@@ -159,7 +165,8 @@ __global__ void k_macro(Geo g, Phys p, const uint8_t *__restrict__ mask,
         if (cy > 0) jy += row[r]; else if (cy < 0) jy -= row[r];
         if (D == 3) { if (cz > 0) jz += row[r]; else if (cz < 0) jz -= row[r]; }
     }
-    const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    const double inv = 1.0 / rho;
+    const double ux = jx * inv, uy = jy * inv, uz = jz * inv;
     if (!(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz))
         atomicOr(status, 1);
     rp[n] = make_double2(rho, signed_psi(p, rho));
@@ -223,15 +230,23 @@ __global__ void k_collide(Geo g, Phys p, const uint8_t *__restrict__ mask,
         S[a][2] = 0.5 * (zs + xs);
     }
     const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
-    const double om = p.omega;
+    // post = f* + (1 - omega)(f - feq); feq and f* by x-y partial products
+    const double omw = 1.0 - p.omega;
+    double Ae[3][3], As[3][3];
+#pragma unroll
+    for (int cx = 0; cx < 3; ++cx) {
+        const double ex = rho * E[0][cx], sx = rho * S[0][cx];
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy) { Ae[cx][cy] = ex * E[1][cy]; As[cx][cy] = sx * S[1][cy]; }
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cxi(i), cy = cyi(i), cz = D == 3 ? czi(i) : 0;
-        double eq = rho * E[0][cx + 1] * E[1][cy + 1];
-        double st = rho * S[0][cx + 1] * S[1][cy + 1];
+        double eq = Ae[cx + 1][cy + 1];
+        double st = As[cx + 1][cy + 1];
         if (D == 3) { eq *= E[2][cz + 1]; st *= S[2][cz + 1]; }
         const double fi = f[(size_t)i * g.N + n];
-        const double post = fi + om * (eq - fi) + (st - eq);
+        const double post = fma(omw, fi - eq, st);
         const unsigned dst = X[cx + 1] + g.nx * (Y[cy + 1] + g.ny * Z[cz + 1]);
         if (mask[dst]) fout[(size_t)(Q - 1 - i) * g.N + n] = post;
         else           fout[(size_t)i * g.N + dst] = post;
