@@ -36,7 +36,8 @@ struct lbm_ctx {
     void *base = nullptr;
     bool owns_base = false;
     size_t bytes = 0;
-    void *fv[2] = {nullptr, nullptr};   // population buffers (double or float)
+    void *fv[2] = {nullptr, nullptr};   // population buffers (double, float or 16-bit)
+    float *rs[2] = {nullptr, nullptr};  // shifted storage: source densities of buffer k
     double2 *rp = nullptr;
     double *u = nullptr, *gflux = nullptr, *partial = nullptr, *sums = nullptr;
     uint8_t *mask = nullptr;
@@ -55,10 +56,15 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, rp, u, g, mask, partial, sums, status, total;
+    size_t f0, f1, rs0, rs1, rp, u, g, mask, partial, sums, status, total;
 };
 
-size_t pop_bytes(int storage) { return storage == LBM_F32 ? sizeof(float) : sizeof(double); }
+bool shifted(int storage) { return storage == LBM_F16S || storage == LBM_BF16S; }
+
+size_t pop_bytes(int storage)
+{
+    return storage == LBM_F64 ? sizeof(double) : storage == LBM_F32 ? sizeof(float) : 2;
+}
 
 Layout layout_for(int D, int Q, size_t N, int storage)
 {
@@ -71,6 +77,9 @@ Layout layout_for(int D, int Q, size_t N, int storage)
                                                                    : sizeof(double) * (1 + 2 * D) * N;
     L.f0 = o; o = align_up(o + fb);
     L.f1 = o; o = align_up(o + fb);
+    const size_t rsb = (storage == LBM_F16S || storage == LBM_BF16S) ? sizeof(float) * N : 0;
+    L.rs0 = o; o = align_up(o + rsb);
+    L.rs1 = o; o = align_up(o + rsb);
     L.rp = o; o = align_up(o + sizeof(double2) * N);
     L.u = o; o = align_up(o + sizeof(double) * D * N);
     L.g = o; o = align_up(o + sizeof(double) * D * N);
@@ -163,6 +172,10 @@ int ensure_memory(lbm_ctx *h)
     char *b = static_cast<char *>(h->base);
     h->fv[0] = b + L.f0;
     h->fv[1] = b + L.f1;
+    if (shifted(h->storage)) {
+        h->rs[0] = reinterpret_cast<float *>(b + L.rs0);
+        h->rs[1] = reinterpret_cast<float *>(b + L.rs1);
+    }
     h->rp = reinterpret_cast<double2 *>(b + L.rp);
     h->u = reinterpret_cast<double *>(b + L.u);
     h->gflux = reinterpret_cast<double *>(b + L.g);
@@ -202,11 +215,37 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
                                                                  dst, h->status);
 }
 
+template <int LAT, typename ST>
+void launch_shifted_t(lbm_ctx *h, cudaStream_t s, int k)
+{
+    static bool attr_set = false;   // once per kernel instance per process
+    const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
+    if (!attr_set) {
+        cudaFuncSetAttribute(lbmf::k_step_shifted<LAT, ST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        attr_set = true;
+    }
+    using L = lbmf::LatF<LAT>;
+    lbmf::k_step_shifted<LAT, ST><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
+        h->rs[k], h->rs[k ^ 1], h->status);
+}
+
+template <int LAT>
+void launch_shifted(lbm_ctx *h, cudaStream_t s, int k)
+{
+    if (h->storage == LBM_F16S) launch_shifted_t<LAT, __half>(h, s, k);
+    else                        launch_shifted_t<LAT, __nv_bfloat16>(h, s, k);
+}
+
 // One time step; returns the number of kernels launched (0 on error).
 template <int LAT>
 int launch_step(lbm_ctx *h, cudaStream_t s, int *nk)
 {
-    if (h->storage == LBM_F32) {
+    if (shifted(h->storage)) {
+        launch_shifted<LAT>(h, s, h->cur);
+        *nk = 1;
+    } else if (h->storage == LBM_F32) {
         launch_fused<LAT>(h, s, f32(h, h->cur), f32(h, h->cur ^ 1));
         *nk = 1;
     } else {
@@ -233,7 +272,56 @@ int step_plain(lbm_ctx *h, cudaStream_t s, int *nk_out = nullptr)
     return rc;
 }
 
-int kernels_per_step(const lbm_ctx *h) { return h->storage == LBM_F32 ? 1 : 2; }
+int kernels_per_step(const lbm_ctx *h) { return h->storage == LBM_F64 ? 2 : 1; }
+
+// Shifted storage I/O goes through a temporary FP64 copy of the populations.
+struct TempF64 {
+    double *p = nullptr;
+    ~TempF64() { if (p) cudaFree(p); }
+};
+
+template <int LAT>
+int decode_to(lbm_ctx *h, int k, double *out)
+{
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    if (h->storage == LBM_F16S)
+        lbmk::k_decode_shifted<LAT, __half><<<gr, bl, 0, h->stream>>>(
+            h->geo, static_cast<const __half *>(h->fv[k]), h->rs[k], out);
+    else
+        lbmk::k_decode_shifted<LAT, __nv_bfloat16><<<gr, bl, 0, h->stream>>>(
+            h->geo, static_cast<const __nv_bfloat16 *>(h->fv[k]), h->rs[k], out);
+    CU(h, cudaGetLastError());
+    h->launches += 1;
+    return LBM_OK;
+}
+
+template <int LAT>
+int encode_from(lbm_ctx *h, const double *f)
+{
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    lbmk::k_density<LAT><<<gr, bl, 0, h->stream>>>(h->geo, f, h->rs[0]);
+    if (h->storage == LBM_F16S)
+        lbmk::k_encode_shifted<LAT, __half><<<gr, bl, 0, h->stream>>>(
+            h->geo, f, h->rs[0], static_cast<__half *>(h->fv[0]));
+    else
+        lbmk::k_encode_shifted<LAT, __nv_bfloat16><<<gr, bl, 0, h->stream>>>(
+            h->geo, f, h->rs[0], static_cast<__nv_bfloat16 *>(h->fv[0]));
+    CU(h, cudaGetLastError());
+    h->launches += 2;
+    h->cur = 0;
+    return LBM_OK;
+}
+
+int temp_alloc(lbm_ctx *h, TempF64 &t)
+{
+    const size_t bytes = sizeof(double) * (size_t)h->Q * h->geo.N;
+    if (cudaMalloc(&t.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        t.p = nullptr;
+        return fail(h, LBM_ENOMEM, "no room for the FP64 copy of shifted populations");
+    }
+    return LBM_OK;
+}
 
 // Two steps (state buffer 0 -> 1 -> 0) captured once on the library's own
 // stream; replayed on the handle's stream.
@@ -286,7 +374,15 @@ template <int LAT>
 int launch_macro_and_out(lbm_ctx *h, double *rho, double *u, double *U)
 {
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
-    if (h->storage == LBM_F32)
+    if (shifted(h->storage)) {
+        TempF64 t;
+        int rc = temp_alloc(h, t);
+        if (!rc) rc = decode_to<LAT>(h, h->cur, t.p);
+        if (rc) return rc;
+        lbmk::k_macro<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, t.p, h->rp, h->u,
+                                                     h->gflux, h->status);
+        CU(h, cudaStreamSynchronize(h->stream));   // before the temporary is freed
+    } else if (h->storage == LBM_F32)
         lbmk::k_macro<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask,
                                                             f32(h, h->cur), h->rp, h->u,
                                                             h->gflux, h->status);
@@ -304,6 +400,20 @@ template <int LAT>
 int launch_init(lbm_ctx *h, const double *rho0, const double *u0)
 {
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    if (shifted(h->storage)) {
+        TempF64 t;
+        int rc = temp_alloc(h, t);
+        if (rc) return rc;
+        lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0, t.p);
+        rc = encode_from<LAT>(h, t.p);
+        if (rc) return rc;
+        lbmk::k_fill_solid<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
+                                                          h->gflux);
+        CU(h, cudaGetLastError());
+        CU(h, cudaStreamSynchronize(h->stream));
+        h->launches += 2;
+        return LBM_OK;
+    }
     if (h->storage == LBM_F32)
         lbmk::k_init<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0,
                                                            f32(h, h->cur));
@@ -331,6 +441,19 @@ int launch_fill_solid(lbm_ctx *h)
 template <int LAT>
 int launch_reduce(lbm_ctx *h)
 {
+    if (shifted(h->storage)) {
+        TempF64 t;
+        int rc = temp_alloc(h, t);
+        if (!rc) rc = decode_to<LAT>(h, h->cur, t.p);
+        if (rc) return rc;
+        lbmk::k_reduce_partial<LAT><<<lbmk::RED_BLOCKS, lbmk::RED_THREADS, 0, h->stream>>>(
+            h->geo, h->mask, t.p, h->partial);
+        lbmk::k_reduce_final<<<1, lbmk::RED_BLOCKS, 0, h->stream>>>(h->partial, h->sums);
+        CU(h, cudaGetLastError());
+        CU(h, cudaStreamSynchronize(h->stream));
+        h->launches += 2;
+        return LBM_OK;
+    }
     if (h->storage == LBM_F32)
         lbmk::k_reduce_partial<LAT, float><<<lbmk::RED_BLOCKS, lbmk::RED_THREADS, 0, h->stream>>>(
             h->geo, h->mask, f32(h, h->cur), h->partial);
@@ -366,7 +489,7 @@ int lbm_default_params(int eos, lbm_params *p)
 
 size_t lbm_required_bytes(int lattice, int nx, int ny, int nz, int storage)
 {
-    if (!valid_shape(lattice, nx, ny, nz) || (storage != LBM_F64 && storage != LBM_F32)) return 0;
+    if (!valid_shape(lattice, nx, ny, nz) || storage < LBM_F64 || storage > LBM_BF16S) return 0;
     const int D = lattice == LBM_D2Q9 ? 2 : 3, Q = lattice == LBM_D2Q9 ? 9 : 27;
     return layout_for(D, Q, (size_t)nx * ny * nz, storage).total;
 }
@@ -382,7 +505,10 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     lbm_params prm;
     if (p) prm = *p;
     else lbm_default_params(eos, &prm);
-    if (prm.storage != LBM_F64 && prm.storage != LBM_F32) return LBM_EINVAL;
+    if (prm.storage < LBM_F64 || prm.storage > LBM_BF16S) return LBM_EINVAL;
+    if (shifted(prm.storage) && solid_mask)
+        for (size_t n = 0; n < (size_t)nx * ny * nz; ++n)
+            if (solid_mask[n]) return LBM_EINVAL;   // shifted storage: lattices without solids
     if (!(prm.a > 0.0) || !(prm.b > 0.0) || !(prm.rho_w > 0.0)) return LBM_EINVAL;
     lbm_ctx *h = new (std::nothrow) lbm_ctx();
     if (!h) return LBM_ENOMEM;
@@ -572,7 +698,15 @@ int lbm_get_populations(lbm_handle h, double *f, int on_device)
     if (rc) return rc;
     if (!f) return LBM_EINVAL;
     const size_t N = h->geo.N, QN = (size_t)h->Q * N;
-    if (h->storage == LBM_F32) {
+    if (shifted(h->storage)) {
+        TempF64 t;
+        rc = temp_alloc(h, t);
+        if (!rc) rc = h->lattice == LBM_D2Q9 ? decode_to<0>(h, h->cur, t.p) : decode_to<1>(h, h->cur, t.p);
+        if (rc) return rc;
+        CU(h, cudaMemcpyAsync(f, t.p, sizeof(double) * QN,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+    } else if (h->storage == LBM_F32) {
         if (on_device) {
             lbmk::k_convert<float, double><<<1024, 256, 0, h->stream>>>(QN, f32(h, h->cur), f);
             CU(h, cudaGetLastError());
@@ -604,7 +738,16 @@ int lbm_set_populations(lbm_handle h, const double *f, int on_device)
     if (rc) return rc;
     const size_t QN = (size_t)h->Q * h->geo.N;
     h->cur = 0;
-    if (h->storage == LBM_F32) {
+    if (shifted(h->storage)) {
+        TempF64 t;
+        rc = temp_alloc(h, t);
+        if (rc) return rc;
+        CU(h, cudaMemcpyAsync(t.p, f, sizeof(double) * QN,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        rc = h->lattice == LBM_D2Q9 ? encode_from<0>(h, t.p) : encode_from<1>(h, t.p);
+        if (rc) return rc;
+        CU(h, cudaStreamSynchronize(h->stream));
+    } else if (h->storage == LBM_F32) {
         if (on_device) {
             lbmk::k_convert<double, float><<<1024, 256, 0, h->stream>>>(QN, f, f32(h, 0));
             CU(h, cudaGetLastError());
@@ -857,13 +1000,19 @@ int lbm_time_kernels(lbm_handle h, int64_t n, double *ms)
     std::vector<cudaEvent_t> ev(3 * n);
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
-    const bool fused = h->storage == LBM_F32;
+    const bool fused = h->storage != LBM_F64;
     for (int64_t k = 0; k < n; ++k) {
         CU(h, cudaEventRecord(ev[3 * k], h->stream));
         if (fused) {
             CU(h, cudaEventRecord(ev[3 * k + 1], h->stream));
-            if (h->lattice == LBM_D2Q9) launch_fused<0>(h, h->stream, f32(h, h->cur), f32(h, h->cur ^ 1));
-            else launch_fused<1>(h, h->stream, f32(h, h->cur), f32(h, h->cur ^ 1));
+            if (shifted(h->storage)) {
+                if (h->lattice == LBM_D2Q9) launch_shifted<0>(h, h->stream, h->cur);
+                else launch_shifted<1>(h, h->stream, h->cur);
+            } else if (h->lattice == LBM_D2Q9) {
+                launch_fused<0>(h, h->stream, f32(h, h->cur), f32(h, h->cur ^ 1));
+            } else {
+                launch_fused<1>(h, h->stream, f32(h, h->cur), f32(h, h->cur ^ 1));
+            }
             h->launches += 1;
         } else {
             const double *src = f64(h, h->cur);
@@ -906,18 +1055,22 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
 {
     int rc = check_ready(h);
     if (rc) return rc;
-    if (h->storage != LBM_F32) {
+    if (h->storage == LBM_F64) {
         if (chunk_out) *chunk_out = 0;
         return LBM_OK;   // the FP64 step has no tile parameters
     }
     if (h->bad) return fail(h, LBM_ESTATE, "state holds a non-finite density; re-initialise");
-    const size_t bytes = sizeof(float) * (size_t)h->Q * h->geo.N;
+    const size_t bytes = pop_bytes(h->storage) * (size_t)h->Q * h->geo.N;
+    const size_t rbytes = shifted(h->storage) ? sizeof(float) * h->geo.N : 0;
     void *save = nullptr;
-    if (cudaMalloc(&save, bytes) != cudaSuccess) {
+    if (cudaMalloc(&save, bytes + rbytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(h, LBM_ENOMEM, "autotune: no room to save the state");
     }
     CU(h, cudaMemcpyAsync(save, h->fv[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    if (rbytes)
+        CU(h, cudaMemcpyAsync(static_cast<char *>(save) + bytes, h->rs[h->cur], rbytes,
+                              cudaMemcpyDeviceToDevice, h->stream));
     const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128};
     const int nz = h->geof.nz;
     int best = h->geof.chunk;
@@ -932,6 +1085,9 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
         if (ms[1] < best_ms) { best_ms = ms[1]; best = c; }
     }
     cudaError_t e = cudaMemcpyAsync(h->fv[0], save, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && rbytes)
+        e = cudaMemcpyAsync(h->rs[0], static_cast<char *>(save) + bytes, rbytes,
+                            cudaMemcpyDeviceToDevice, h->stream);
     cudaStreamSynchronize(h->stream);
     cudaFree(save);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "autotune restore: %s", cudaGetErrorString(e));

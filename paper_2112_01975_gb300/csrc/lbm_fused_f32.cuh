@@ -13,10 +13,28 @@
 // second read of a node are served from L2.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace lbmf {
+
+// Storage of populations: float (FP32), or 16-bit values of the shift
+// h_i = f_i - w_i rho(src) with rho(src) the FP32 density of the node that
+// pushed the population (the node itself after a bounce-back).
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename ST> __device__ __forceinline__ ST from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v)
+{
+    return __float2bfloat16_rn(v);
+}
+template <typename ST> struct IsShifted { static constexpr bool value = true; };
+template <> struct IsShifted<float> { static constexpr bool value = false; };
 
 struct GeoF {
     int nx, ny, nz;   // as stored; D2Q9: ny = 1 and nz = the 2D y extent
@@ -45,6 +63,14 @@ template <> struct LatF<1> {
     __device__ static constexpr int cy(int i) { return (i / 3) % 3 - 1; }
     __device__ static constexpr int cz(int i) { return i / 9 - 1; }
 };
+
+// Lattice weight w_i = prod of 1D weights 2/3 (c = 0), 1/6 (c = +-1) (Eq. wi).
+template <int LAT> __device__ __forceinline__ constexpr float weight_f(int i)
+{
+    using L = LatF<LAT>;
+    return (L::cx(i) ? 1.0f / 6.0f : 2.0f / 3.0f) * (LAT == 1 ? (L::cy(i) ? 1.0f / 6.0f : 2.0f / 3.0f) : 1.0f) *
+           (L::cz(i) ? 1.0f / 6.0f : 2.0f / 3.0f);
+}
 
 // P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 equations of state).
 __device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
@@ -86,14 +112,56 @@ template <int LAT> struct SharedF {
     int xw[AX], yw[AY];      // wrapped halo coordinates
 };
 
+// Shifted 16-bit storage also keeps the source densities of the planes in
+// flight on a 3-node halo (the sources of the 2-halo's populations).
+template <int LAT> struct SharedS : SharedF<LAT> {
+    static constexpr int RX = SharedF<LAT>::AX + 2, RY = LAT == 1 ? SharedF<LAT>::AY + 2 : 1;
+    static constexpr int QS = 8;   // ring slots (planes pl-4 .. pl+2 live)
+    float rs[QS][RY][RX];
+    int rxw[RX], ryw[RY];
+};
+
+// Population i of the node at halo coordinates (r, c) of ring plane q:
+// stored value plus w_i times the density of its source node.
+template <int LAT, typename ST, typename SM>
+__device__ __forceinline__ float decode_pop(ST hv, int i, int r, int c, int q, const SM &sm)
+{
+    if constexpr (IsShifted<ST>::value) {
+        using L = LatF<LAT>;
+        const int rr = r + (LAT == 1 ? 1 : 0) - L::cy(i), cc = c + 1 - L::cx(i);
+        return to_f(hv) + weight_f<LAT>(i) * sm.rs[(q - L::cz(i) + SM::QS) & (SM::QS - 1)][rr][cc];
+    } else {
+        return to_f(hv);
+    }
+}
+
+// Source densities of one plane (ring index q) on the 3-halo into the ring.
+template <int LAT, typename SM>
+__device__ __forceinline__ void load_rho_plane(SM &sm, const GeoF &g, const float *__restrict__ rho_src,
+                                               int z0, int q)
+{
+    constexpr int RX = SM::RX, RY = SM::RY, QS = SM::QS;
+    constexpr int NT = LatF<LAT>::TX * LatF<LAT>::TY;
+    const int zq = ((z0 - 2 + q) % g.nz + g.nz) % g.nz;
+    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
+    for (int k = threadIdx.x; k < RX * RY; k += NT) {
+        const int r = k / RX, c = k - r * RX;
+        sm.rs[(q + QS) & (QS - 1)][r][c] =
+            __ldg(rho_src + ((unsigned)sm.rxw[c] + (unsigned)g.nx * (unsigned)sm.ryw[r] + plane * (unsigned)zq));
+    }
+}
+
 // One CTA's work: the column tile (bx, by) over the plane chunk bz.
-template <int LAT, bool MASK>
+template <int LAT, bool MASK, typename ST = float, typename SM = SharedF<LAT>>
 __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                                            const uint8_t *__restrict__ mask,
-                                           const float *__restrict__ f, float *__restrict__ fout,
+                                           const ST *__restrict__ f, ST *__restrict__ fout,
                                            int *__restrict__ status, int bx, int by, int bz,
-                                           SharedF<LAT> &sm)
+                                           SM &sm, const float *__restrict__ rho_src = nullptr,
+                                           float *__restrict__ rho_dst = nullptr)
 {
+    constexpr bool SHIFT = IsShifted<ST>::value;
+    static_assert(!(SHIFT && MASK), "shifted storage runs lattices without solid nodes");
     using L = LatF<LAT>;
     constexpr int Q = L::Q, TX = L::TX, TY = L::TY, HY = L::HY;
     constexpr bool THREE = LAT == 1;
@@ -117,6 +185,15 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
     const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
     for (int c = tid; c < AX; c += NT) s_xw[c] = ((x0 - 2 + c) % g.nx + g.nx) % g.nx;
     for (int r = tid; r < AY; r += NT) s_yw[r] = THREE ? ((y0 - HY + r) % g.ny + g.ny) % g.ny : 0;
+    if constexpr (SHIFT) {
+        for (int c = tid; c < SM::RX; c += NT) sm.rxw[c] = ((x0 - 3 + c) % g.nx + g.nx) % g.nx;
+        for (int r = tid; r < SM::RY; r += NT)
+            sm.ryw[r] = THREE ? ((y0 - HY - 1 + r) % g.ny + g.ny) % g.ny : 0;
+        __syncthreads();
+        load_rho_plane<LAT>(sm, g, rho_src, z0, -1);
+        load_rho_plane<LAT>(sm, g, rho_src, z0, 0);
+        load_rho_plane<LAT>(sm, g, rho_src, z0, 1);
+    }
     __syncthreads();
 
     // Planes z0-2 .. z1+1 enter the rings one per iteration; plane z0-2+pl
@@ -135,6 +212,7 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
             float fi[KA][Q];
             unsigned nk[KA];
             bool live[KA], solid[KA];
+            if constexpr (SHIFT) load_rho_plane<LAT>(sm, g, rho_src, z0, pl + 2);   // for the next iteration
 #pragma unroll
             for (int u = 0; u < KA; ++u) {
                 const int k = tid + u * NT;
@@ -145,7 +223,7 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                 solid[u] = MASK && live[u] && mask[nk[u]];
                 if (live[u] && !solid[u]) {
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) fi[u][i] = __ldg(f + (i * N + nk[u]));
+                    for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
                 }
             }
 #pragma unroll
@@ -209,12 +287,13 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                 // the node's own populations (second read, an L2 hit), issued first
                 float fi[Q];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) fi[i] = __ldg(f + (i * N + n));
+                for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
                 const int cr = ty + HY, cc = tx + 2;
                 const float2 c0 = s_rp[pc % RS][cr][cc];
                 const float rho = c0.x;
                 const float spsi = s_sg[pc % RS][ty][tx] * c0.y;
                 if (!(rho > 0.0f) || !isfinite(rho)) atomicOr(status, 1);
+                if constexpr (SHIFT) rho_dst[n] = rho;   // source density of what this node pushes
                 // Korteweg force (Eq. Kforce_final, sign as the force on the fluid).
                 // Per ring s, the pairs (|psi|, rho) of neighbours with c_a = +1 and
                 // c_a = -1 are summed by weight class (centre, edge, corner).
@@ -327,11 +406,12 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
                     const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
-                    const float post = fmaf(p.omw, fi[i] - es.x, es.y);
+                    const float post = SHIFT ? fmaf(p.omw, fi[i] - es.x, es.y) - weight_f<LAT>(i) * rho
+                                             : fmaf(p.omw, fi[i] - es.x, es.y);
                     const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
                                          plane * (unsigned)Z[cz + 1];
-                    if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = post;
-                    else                   fout[i * N + dst] = post;
+                    if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = from_f<ST>(post);
+                    else                   fout[i * N + dst] = from_f<ST>(post);
                 }
             }
         }
@@ -345,6 +425,21 @@ k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__res
 {
     __shared__ SharedF<LAT> sm;
     fused_tile<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+}
+
+// Shifted 16-bit storage (ST = __half or __nv_bfloat16): populations h_i
+// with the source densities rho_src read and rho_dst written; dynamic shared
+// memory of sizeof(SharedS<LAT>).
+template <int LAT, typename ST>
+__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
+k_step_shifted(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
+               const float *__restrict__ rho_src, float *__restrict__ rho_dst,
+               int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
+    fused_tile<LAT, false, ST, SharedS<LAT>>(g, p, nullptr, f, fout, status, blockIdx.x, blockIdx.y,
+                                            blockIdx.z, sm, rho_src, rho_dst);
 }
 
 // Many lattices of one type in one launch: descriptor of one member for the

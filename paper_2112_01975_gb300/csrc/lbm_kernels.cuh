@@ -406,6 +406,64 @@ k_reduce_final(const double *__restrict__ partial, double *__restrict__ out)
     }
 }
 
+// Shifted 16-bit storage (h_i = f_i - w_i rho(src), src = r - c_i, or r itself
+// when r - c_i is solid): decode to FP64, per-node densities, encode.
+__device__ __forceinline__ double weight_d(int i, int D)
+{
+    const double w1[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    return w1[cxi(i) + 1] * w1[cyi(i) + 1] * (D == 3 ? w1[czi(i) + 1] : 1.0);
+}
+
+__device__ __forceinline__ unsigned source_node(const Geo &g, int D, int i, int x, int y, int z)
+{
+    const int sx = (x - cxi(i) + g.nx) % g.nx, sy = (y - cyi(i) + g.ny) % g.ny;
+    const int sz = D == 3 ? (z - czi(i) + g.nz) % g.nz : 0;
+    return sx + g.nx * (sy + g.ny * sz);
+}
+
+template <int LAT, typename ST>
+__global__ void k_decode_shifted(Geo g, const ST *__restrict__ h, const float *__restrict__ rho_src,
+                                 double *__restrict__ f)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        f[(size_t)i * g.N + n] = (double)lbmf::to_f(h[(size_t)i * g.N + n]) +
+                                 weight_d(i, D) * (double)rho_src[source_node(g, D, i, x, y, z)];
+}
+
+template <int LAT>
+__global__ void k_density(Geo g, const double *__restrict__ f, float *__restrict__ rho)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const unsigned n = x + g.nx * (blockIdx.y + g.ny * blockIdx.z);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) s += f[(size_t)i * g.N + n];
+    rho[n] = (float)s;
+}
+
+template <int LAT, typename ST>
+__global__ void k_encode_shifted(Geo g, const double *__restrict__ f, const float *__restrict__ rho,
+                                 ST *__restrict__ h)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        h[(size_t)i * g.N + n] = lbmf::from_f<ST>(
+            (float)(f[(size_t)i * g.N + n] - weight_d(i, D) * (double)rho[source_node(g, D, i, x, y, z)]));
+}
+
 // Element-wise type conversion (population I/O of FP32 storage).
 template <typename A, typename B>
 __global__ void k_convert(size_t n, const A *__restrict__ in, B *__restrict__ out)

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 
 D2Q9, D3Q27 = 0, 1
 EOS_VDW, EOS_PR, EOS_RKS, EOS_CS = 0, 1, 2, 3
-F64, F32 = 0, 1
+F64, F32, F16S, BF16S = 0, 1, 2, 3
 FLAG_PHI_OFF = 1
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
           5: "LBM_ETIMEOUT", 6: "LBM_ESTATE", 7: "LBM_ETOOBIG"}
