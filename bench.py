@@ -34,6 +34,11 @@ ALG_BYTES_PER_LU = {  # populations read once and written once per lattice updat
     (0, "f64"): 2 * 9 * 8,
     (1, "f32"): 2 * 27 * 4,
     (0, "f32"): 2 * 9 * 4,
+    # 16-bit populations plus the 4-byte source density read and written
+    (1, "f16s"): 2 * 27 * 2 + 8,
+    (0, "f16s"): 2 * 9 * 2 + 8,
+    (1, "bf16s"): 2 * 27 * 2 + 8,
+    (0, "bf16s"): 2 * 9 * 2 + 8,
 }
 # FP64 flops per node executed by the collide kernel (D3Q27), counted from
 # the source: two stencil rings 244 (13 neighbour-pair differences of two
@@ -50,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d3q27_drop_128^3_pr_tr0.7")
-    ap.add_argument("--storage", default="f32", choices=["f64", "f32"])
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
@@ -272,12 +277,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     stream = torch.cuda.Stream()
-    storage = F32 if args.storage == "f32" else F64
+    from paper_2112_01975_gb300.lbm import BF16S, F16S
+    storage = {"f64": F64, "f32": F32, "f16s": F16S, "bf16s": BF16S}[args.storage]
     g = LBM(w.lattice, w.nx, w.ny, w.nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
             stream=stream, storage=storage)
     rho0 = w.rho0()
     g.init(rho0)
-    if storage == F32:
+    chunk = 0
+    if storage != F64:
         chunk = args.chunk or g.autotune()
         g.set_chunk(chunk)
     g.step(args.warmup)
@@ -292,17 +299,23 @@ def main():
     peak, peak_kind = measured_peaks()
     alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * w.nodes
     achieved = alg / (ms_collide * 1e-3) / 1e9
-    if storage == F32:
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
+    # fused step on this 128^3 workload (FP32: 260.3 + 188.3 MB; FP16
+    # shifted: 137.7 + 85.0 MB)
+    traffic_fused = {"f32": 448.66e6, "f16s": 222.67e6}.get(args.storage) \
+        if w.name == "d3q27_drop_128^3_pr_tr0.7" else None
+    if storage != F64:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_step_f32 (fused step)", "peak_source": peak_kind + " hbm_gbs",
+                    "frac": achieved / peak, "traffic": traffic_fused,
+                    "kernel": "k_step_f32 (fused step)" if storage == F32 else "k_step_shifted",
+                    "peak_source": peak_kind + " hbm_gbs",
                     "alg_bytes_per_launch": alg, "ms_per_launch": ms_collide,
                     "chunk": chunk}
     else:
         tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                    "traffic": 402.24e6 * w.nodes / 884736 if w.lattice == 1 else None,
+                    "traffic": 403.36e6 * w.nodes / 884736 if w.lattice == 1 else None,
                     "kernel": "k_collide (FP64)",
                     "peak_source": "nominal FP64 rate of GB300 (recipe table)",
                     "flops_per_node": COLLIDE_FP64_FLOPS_PER_NODE,
@@ -364,7 +377,8 @@ def main():
                    "nodes": w.nodes, "storage": args.storage,
                    "eos": "Peng-Robinson" if w.eos == 1 else "vdW",
                    "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (
-                       (27 if w.lattice else 9) * (8 if args.storage == "f64" else 4) * w.nodes / 1e6),
+                       (27 if w.lattice else 9) * {"f64": 8, "f32": 4}.get(args.storage, 2)
+                       * w.nodes / 1e6),
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "cpu_baseline": cpu,
