@@ -49,6 +49,7 @@ def lib():
         L.oracle_fstar.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp, _dp]
         L.oracle_stencil.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
         L.oracle_weights.argtypes = [C.c_void_p, _dp, C.POINTER(C.c_int)]
+        L.oracle_post_local.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
         L.oracle_rt.restype = C.c_double
         L.oracle_rt.argtypes = [C.c_void_p]
         L.oracle_alpha.restype = C.c_double
@@ -184,6 +185,15 @@ class OracleLBM:
         c = np.empty(3 * self.Q, dtype=np.int32)
         lib().oracle_weights(self._h, _p(w), c.ctypes.data_as(C.POINTER(C.c_int)))
         return w, c.reshape(self.Q, 3)
+
+    def post_local(self, block: np.ndarray, mblock: np.ndarray) -> np.ndarray:
+        """Post-collision populations of the centre of a 5x5(x5) block of
+        populations block[dz][dy][dx][i] with solid flags mblock[dz][dy][dx]."""
+        b = np.ascontiguousarray(block, dtype=np.float64)
+        m = np.ascontiguousarray(mblock, dtype=np.uint8)
+        out = np.empty(self.Q)
+        lib().oracle_post_local(self._h, _p(b), m.ctypes.data_as(C.c_void_p), _p(out))
+        return out
 
     @property
     def RT(self) -> float:

@@ -417,3 +417,77 @@ void oracle_eos_pressure_array(int eos, double a, double b, double RT, double al
 {
     for (long k = 0; k < n; ++k) out[k] = oracle_eos_pressure(eos, a, b, RT, alpha, rho[k]);
 }
+
+/* One node's post-collision populations from its local neighbourhood, for
+ * checking large lattices at sampled nodes. block[((dz*5 + dy)*5 + dx)*Q + i]
+ * holds the populations of the node at offset (dx-2, dy-2, dz-2) (dz = 2 only
+ * for D2Q9), mblock the matching solid flags. The same steps as a full step
+ * (moments, EOS and pseudo-potential, Eq. Kforce_final stencils, Eq.
+ * correction, product-form collision) restricted to what the centre needs.
+ * out[i] = post-collision population i of the centre node. */
+void oracle_post_local(const oracle_ctx *o, const double *block, const unsigned char *mblock,
+                       double *out)
+{
+    const int Q = o->Q, D = o->D;
+    const int nz5 = D == 3 ? 5 : 1;
+    double rho[125], u[3][125], psi[125];
+    int sgn[125];
+    for (int k = 0; k < 125; ++k) { rho[k] = 0.0; psi[k] = 0.0; sgn[k] = -1; u[0][k] = u[1][k] = u[2][k] = 0.0; }
+#define LIDX(dx, dy, dz) ((((D == 3 ? (dz) + 2 : 0) * 5 + (dy) + 2) * 5) + (dx) + 2)
+    for (int bz = 0; bz < nz5; ++bz)
+        for (int by = 0; by < 5; ++by)
+            for (int bx = 0; bx < 5; ++bx) {
+                int k = (bz * 5 + by) * 5 + bx;
+                if (mblock[k]) {
+                    rho[k] = o->rho_w;
+                } else {
+                    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+                    for (int i = 0; i < Q; ++i) {
+                        double fi = block[(long)k * Q + i];
+                        r += fi;
+                        for (int al = 0; al < D; ++al) j[al] += o->c[i][al] * fi;
+                    }
+                    rho[k] = r;
+                    for (int al = 0; al < D; ++al) u[al][k] = j[al] / r;
+                }
+                double P = oracle_eos_pressure(o->eos, o->a, o->b, o->RT, o->alpha, rho[k]);
+                double P0 = rho[k] / 3.0;
+                psi[k] = P > P0 ? sqrt(P - P0) : sqrt(P0 - P);
+                sgn[k] = P > P0 ? 1 : -1;
+            }
+    const int c0 = LIDX(0, 0, 0);
+    /* force at the centre: the two stencils of Eq. Kforce_final, force on the fluid */
+    double Spsi[3] = {0.0, 0.0, 0.0}, Srho[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        const int *c = o->c[i];
+        int k1 = LIDX(c[0], c[1], c[2]), k2 = LIDX(2 * c[0], 2 * c[1], 2 * c[2]);
+        double vp = (4.0 / 3.0) * psi[k1] + (-1.0 / 6.0) * psi[k2];
+        double vr = 2.0 * rho[k1] + (-1.0) * rho[k2];
+        for (int al = 0; al < D; ++al) {
+            Spsi[al] += (o->w[i] * 3.0) * c[al] * vp;
+            Srho[al] += (o->w[i] * 3.0) * c[al] * vr;
+        }
+    }
+    double fs = (o->flags & ORACLE_FORCE_PRINTED_SIGN) ? 1.0 : -1.0;
+    double F[3] = {0.0, 0.0, 0.0}, Phi[3] = {0.0, 0.0, 0.0}, uc[3] = {0.0, 0.0, 0.0};
+    double pref = (o->flags & ORACLE_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * o->omega);
+    if (o->flags & ORACLE_PHI_PRINTED_SIGN) pref = -pref;
+    for (int al = 0; al < D; ++al) {
+        F[al] = fs * (sgn[c0] * 2.0 * psi[c0] * Spsi[al] + o->kappa * rho[c0] * Srho[al]);
+        int e[3] = {0, 0, 0};
+        e[al] = 1;
+        int kp = LIDX(e[0], e[1], e[2]), km = LIDX(-e[0], -e[1], -e[2]);
+        double gp = rho[kp] * u[al][kp] * u[al][kp] * u[al][kp];
+        double gm = rho[km] * u[al][km] * u[al][km] * u[al][km];
+        Phi[al] = pref * 0.5 * (gp - gm);
+        uc[al] = u[al][c0];
+    }
+    double feq[27], fst[27];
+    oracle_feq(o, rho[c0], uc, feq);
+    oracle_fstar(o, rho[c0], uc, F, Phi, fst);
+    for (int i = 0; i < Q; ++i) {
+        double fi = block[(long)c0 * Q + i];
+        out[i] = fi + o->omega * (feq[i] - fi) + (fst[i] - feq[i]);
+    }
+#undef LIDX
+}

@@ -247,3 +247,30 @@ def test_mirror_symmetry():
     rb, ub, _, _ = b.moments()
     assert np.allclose(rb.reshape(n, n)[:, ::-1], ra.reshape(n, n), rtol=1e-12)
     assert np.allclose(-ub[: n * n].reshape(n, n)[:, ::-1], ua[: n * n].reshape(n, n), atol=1e-13)
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_node_local_post_matches_full_step(lattice):
+    """oracle_post_local on a node's neighbourhood gives exactly the values the
+    full oracle step pushes from that node (bounce-back included)."""
+    from oracle import sample
+    from paper_2112_01975_gb300.inputs import add_noise, block_mask, drop
+    n = 12
+    nz = 1 if lattice == 0 else 10
+    mask = block_mask(n, n, nz, (0, 0, 0), (n, 2, nz))          # a wall at y = 0, 1
+    o = OracleLBM(lattice, n, n, nz, 0, 0.8, 0.0255116, 0.9, a=9 / 490, mask=mask, rho_w=0.84)
+    rho = add_noise(drop(n, n, nz, 3.5, 0.8388, 6.7645), 1e-3, 13)
+    u0 = 0.02 * np.random.default_rng(3).uniform(-1, 1, o.D * o.N)
+    o.init(np.where(mask == 1, 1.0, rho), u0)
+    o.step(3)
+    f = o.get_populations().reshape(o.Q, -1)
+    o.step(1)
+    f1 = o.get_populations().reshape(o.Q, -1)
+    _, c = o.weights()
+    shape = (nz, n, n)
+    for (x, y, z) in [(5, 5, 0), (0, 2, nz - 1), (11, 3, nz // 2), (6, 11, min(1, nz - 1))]:
+        idx = sample.block_indices(shape, x, y, z, o.D)
+        block = f[:, idx].T
+        post = o.post_local(block, mask[idx])
+        for i, (j, d) in enumerate(sample.pushed_indices(shape, x, y, z, c, mask)):
+            assert post[i] == pytest.approx(f1[j, d], rel=1e-14, abs=1e-16)
