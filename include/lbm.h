@@ -125,9 +125,16 @@ int lbm_bind_device_memory(lbm_handle h, void *dev, size_t bytes);
  * handle's own stream, created by lbm_create). */
 int lbm_set_stream(lbm_handle h, void *stream);
 
-/* Set populations to the equilibrium f_eq(rho0, u0) (Eq. LBMeq) at fluid
- * nodes. rho0: double[N] (> 0 at fluid nodes); u0: double[D*N] or NULL
- * for zero. on_device: 0 if the pointers are host memory, 1 if device.
+/* Set the initial populations at fluid nodes to the equilibrium of Eq. LBMeq
+ * at density rho0 and bare velocity u = U0 - F/(2 rho0), where F is the
+ * Korteweg force of the density field rho0 (Eq. Kforce_final, solid nodes at
+ * rho_w), so that the physical velocity U = u + F/(2 rho) of Sec. 2.3.5 (the
+ * U of lbm_moments) equals U0 at t = 0. The paper gives no initial
+ * populations; starting from f_eq(rho0, U0) instead would give every
+ * interface an initial velocity F/(2 rho). Solid nodes get zero populations.
+ * rho0: double[N] (> 0 at fluid nodes); u0: double[D*N], component-major
+ * (U0_x of all nodes, then U0_y[, U0_z]), or NULL for U0 = 0.
+ * on_device: 0 if the pointers are host memory, 1 if device.
  * Allocates the device memory on first use unless bound. */
 int lbm_init(lbm_handle h, const double *rho0, const double *u0, int on_device);
 

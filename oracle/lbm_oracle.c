@@ -44,6 +44,9 @@
  *    magnitude, the sign comes from the centre node.
  *  - Solid nodes carry the virtual density rho_w (Sec. 4.5) in both
  *    stencils, u = 0, and are never collided or streamed.
+ *  - Initial populations (the paper gives none): the equilibrium at the bare
+ *    velocity u = U0 - F(rho0)/(2 rho0), so that the flow starts with the
+ *    requested physical velocity U0 (oracle_init).
  *
  * Lattice units: dr = dt = 1, cs2 = 1/3, R = 1.
  * Direction index i = (cx+1) + 3(cy+1) [+ 9(cz+1)], opposite = Q-1-i.
@@ -238,27 +241,11 @@ void oracle_stencil(const oracle_ctx *o, const double *g, double g1, double g2, 
             }
 }
 
-/* Steps 1-4 of the update on the current populations: rho, u, P, psi, s, F, Phi. */
-static void macroscopic(oracle_ctx *o)
+/* Steps 2-3 on the density field o->rho (rho_w at solid nodes): P, psi, s, F. */
+static void force_from_density(oracle_ctx *o)
 {
     long N = o->N;
-    int Q = o->Q, D = o->D;
-    /* moments, Sec. 2.3.3 */
-    for (long n = 0; n < N; ++n) {
-        if (o->mask[n]) {
-            o->rho[n] = o->rho_w;
-            for (int al = 0; al < 3; ++al) o->u[al * N + n] = 0.0;
-            continue;
-        }
-        double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
-        for (int i = 0; i < Q; ++i) {
-            double fi = o->f[(long)i * N + n];
-            rho += fi;
-            for (int al = 0; al < D; ++al) j[al] += o->c[i][al] * fi;
-        }
-        o->rho[n] = rho;
-        for (int al = 0; al < 3; ++al) o->u[al * N + n] = al < D ? j[al] / rho : 0.0;
-    }
+    int D = o->D;
     /* equation of state and pseudo-potential, Sec. 2.3.4 with P0 = rho/3 */
     for (long n = 0; n < N; ++n) {
         double rho = o->rho[n];
@@ -281,6 +268,30 @@ static void macroscopic(oracle_ctx *o)
         }
     free(Spsi);
     free(Srho);
+}
+
+/* Steps 1-4 of the update on the current populations: rho, u, P, psi, s, F, Phi. */
+static void macroscopic(oracle_ctx *o)
+{
+    long N = o->N;
+    int Q = o->Q, D = o->D;
+    /* moments, Sec. 2.3.3 */
+    for (long n = 0; n < N; ++n) {
+        if (o->mask[n]) {
+            o->rho[n] = o->rho_w;
+            for (int al = 0; al < 3; ++al) o->u[al * N + n] = 0.0;
+            continue;
+        }
+        double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < Q; ++i) {
+            double fi = o->f[(long)i * N + n];
+            rho += fi;
+            for (int al = 0; al < D; ++al) j[al] += o->c[i][al] * fi;
+        }
+        o->rho[n] = rho;
+        for (int al = 0; al < 3; ++al) o->u[al * N + n] = al < D ? j[al] / rho : 0.0;
+    }
+    force_from_density(o);
     /* correction term, Eq. correction with P0 = rho/3 (sign reading in the header) */
     double pref = (o->flags & ORACLE_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * o->omega);
     if (o->flags & ORACLE_PHI_PRINTED_SIGN) pref = -pref;
@@ -337,19 +348,27 @@ static void step_once(oracle_ctx *o)
     double *t = o->f; o->f = o->fnew; o->fnew = t;
 }
 
-/* Populations f = f_eq(rho0, u0) at fluid nodes, 0 at solid nodes. */
+/* Populations at rest in the physical velocity: f = f_eq(rho0, U0 - F/(2 rho0))
+ * at fluid nodes, with F the force of the density field rho0 (Eq. Kforce_final),
+ * so that U = u + F/(2 rho) (Sec. 2.3.5) equals U0 at t = 0; 0 at solid nodes.
+ * The paper does not state its initial populations; f_eq(rho0, U0) would start
+ * every interface with U = F/(2 rho) != 0, an impulse that at large density
+ * ratios sends a pressure wave into the liquid. u0 NULL means U0 = 0. */
 void oracle_init(oracle_ctx *o, const double *rho0, const double *u0)
 {
     long N = o->N;
     double feq[27];
     memset(o->fnew, 0, sizeof(double) * o->Q * N);
+    for (long n = 0; n < N; ++n) o->rho[n] = o->mask[n] ? o->rho_w : rho0[n];
+    force_from_density(o);
     for (long n = 0; n < N; ++n) {
-        double u[3] = {0.0, 0.0, 0.0};
-        for (int al = 0; al < o->D; ++al) u[al] = u0 ? u0[al * N + n] : 0.0;
         if (o->mask[n]) {
             for (int i = 0; i < o->Q; ++i) o->f[(long)i * N + n] = 0.0;
             continue;
         }
+        double u[3] = {0.0, 0.0, 0.0};
+        for (int al = 0; al < o->D; ++al)
+            u[al] = (u0 ? u0[al * N + n] : 0.0) - o->F[al * N + n] / (2.0 * rho0[n]);
         oracle_feq(o, rho0[n], u, feq);
         for (int i = 0; i < o->Q; ++i) o->f[(long)i * N + n] = feq[i];
     }

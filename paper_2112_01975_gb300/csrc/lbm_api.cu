@@ -400,30 +400,29 @@ template <int LAT>
 int launch_init(lbm_ctx *h, const double *rho0, const double *u0)
 {
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    // side fields first: the initial force needs rho and s psi of every node
+    lbmk::k_fill_solid<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
+                                                      h->gflux);
+    lbmk::k_init_density<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, h->rp);
+    h->launches += 3;
     if (shifted(h->storage)) {
         TempF64 t;
         int rc = temp_alloc(h, t);
         if (rc) return rc;
-        lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0, t.p);
+        lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, u0, t.p);
         rc = encode_from<LAT>(h, t.p);
         if (rc) return rc;
-        lbmk::k_fill_solid<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
-                                                          h->gflux);
         CU(h, cudaGetLastError());
-        CU(h, cudaStreamSynchronize(h->stream));
-        h->launches += 2;
+        CU(h, cudaStreamSynchronize(h->stream));   // before the temporary is freed
         return LBM_OK;
     }
     if (h->storage == LBM_F32)
-        lbmk::k_init<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0,
+        lbmk::k_init<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, u0,
                                                            f32(h, h->cur));
     else
-        lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, rho0, u0,
+        lbmk::k_init<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, u0,
                                                     f64(h, h->cur));
-    lbmk::k_fill_solid<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, h->rp, h->u,
-                                                      h->gflux);
     CU(h, cudaGetLastError());
-    h->launches += 2;
     return LBM_OK;
 }
 

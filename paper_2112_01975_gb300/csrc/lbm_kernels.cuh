@@ -286,11 +286,28 @@ __global__ void k_moments_out(Geo g, Phys p, const uint8_t *__restrict__ mask,
     }
 }
 
-// Equilibrium populations from (rho0, u0) at fluid nodes, zero at solid nodes;
-// solid nodes' side fields get rho_w and zero velocity.
+// Side field of the initial density: rp = (rho0, s psi(rho0)) at fluid nodes
+// (solid nodes get theirs from k_fill_solid).
+template <int LAT>
+__global__ void k_init_density(Geo g, Phys p, const uint8_t *__restrict__ mask,
+                               const double *__restrict__ rho0, double2 *__restrict__ rp)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+    if (mask[n]) return;
+    const double rho = rho0[n];
+    rp[n] = make_double2(rho, signed_psi(p, rho));
+}
+
+// Initial populations at rest in the physical velocity: the equilibrium at
+// the bare velocity u = U0 - F/(2 rho0), F the Korteweg force of the initial
+// density (rp, filled by k_init_density and k_fill_solid), so that
+// U = u + F/(2 rho) of Sec. 2.3.5 equals U0 at t = 0. Zero at solid nodes.
 template <int LAT, typename T = double>
 __global__ void k_init(Geo g, Phys p, const uint8_t *__restrict__ mask,
-                       const double *__restrict__ rho0, const double *__restrict__ u0,
+                       const double2 *__restrict__ rp, const double *__restrict__ u0,
                        T *__restrict__ f)
 {
     constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
@@ -303,11 +320,14 @@ __global__ void k_init(Geo g, Phys p, const uint8_t *__restrict__ mask,
         for (int i = 0; i < Q; ++i) f[(size_t)i * g.N + n] = (T)0;
         return;
     }
-    const double rho = rho0[n];
+    const double2 c = rp[n];
+    const double rho = c.x;
+    double F[3] = {0.0, 0.0, 0.0};
+    korteweg_force<LAT>(g, p, rp, x, y, z, rho, c.y, F);
     double E[3][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const double ua = u0 ? u0[a * g.N + n] : 0.0;
+        const double ua = (u0 ? u0[a * g.N + n] : 0.0) - F[a] / (2.0 * rho);
         const double ze = 1.0 / 3.0 + ua * ua;
         E[a][0] = 0.5 * (ze - ua);
         E[a][1] = 1.0 - ze;

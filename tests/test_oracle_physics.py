@@ -7,13 +7,16 @@
   link beyond the last fluid node.
 - Normal-mode decay independent of the frame velocity with the correction
   Phi, frame-dependent without it or with the printed sign (Sec. 4.2).
+- The initial state has the requested physical velocity U (Sec. 2.3.5), and
+  a large-density-ratio drop started at rest in U stays bounded where the
+  impulsive start diverges.
 """
 import numpy as np
 import pytest
 
 from oracle import physics as ph
 from oracle.lbm import EOS, FORCE_PRINTED_SIGN, OracleLBM, PHI_OFF, PHI_PRINTED_SIGN
-from paper_2112_01975_gb300.inputs import slab
+from paper_2112_01975_gb300.inputs import drop, slab
 
 A_VDW = 9 / 490
 
@@ -123,3 +126,54 @@ def test_correction_restores_galilean_invariance():
     assert _acoustic_rate(0.2, 0) == pytest.approx(g0, rel=3e-3)
     assert abs(_acoustic_rate(0.2, PHI_OFF) / g0 - 1) > 0.1
     assert abs(_acoustic_rate(0.2, PHI_PRINTED_SIGN) / g0 - 1) > 0.2
+
+
+def _drop_state(t_over_tc, a, n, R, tau):
+    e = EOS(0, t_over_tc, a=a)
+    rv, rl, ps = ph.maxwell(e)
+    kap = ph.kappa_for_width(e, 5.0, (rv, rl, ps))
+    o = OracleLBM(0, n, n, 1, 0, t_over_tc, kap, tau, a=a)
+    return o, drop(n, n, 1, R, rv, rl, 5.0), rv, rl
+
+
+def test_init_starts_at_the_requested_physical_velocity():
+    """U = u + F/(2 rho) (Sec. 2.3.5) equals the U0 passed to init, at rest
+    and in uniform motion, across an interface where F/rho is not small."""
+    o, rho0, _, _ = _drop_state(0.8, A_VDW, 48, 12.0, 1.0)
+    N = o.N
+    o.init(rho0)
+    _, u, U, F = o.moments()
+    assert np.max(np.abs(F[:N] / rho0)) > 1e-3
+    assert np.max(np.abs(U)) < 1e-15
+    assert np.max(np.abs(u + F / (2 * np.tile(rho0, 2)))) < 1e-15
+    U0 = np.concatenate([np.full(N, 0.02), np.full(N, -0.01)])
+    o.init(rho0, U0)
+    _, _, U, _ = o.moments()
+    assert np.max(np.abs(U - U0)) < 1e-15
+
+
+def test_rest_start_holds_a_large_density_ratio_drop():
+    """A drop at T/Tc = 0.36 (density ratio 1.2e3, the state of the
+    dynamic cases of Sec. 6) at nu = 0.075 with W = 5 stays bounded and
+    near coexistence when it starts at rest in U. Started with bare u = 0
+    instead (U0 = F/(2 rho0)), the interface's inward pressure wave drives
+    the liquid past the EOS pole 1/b and the run diverges."""
+    a, tau = 0.0017375254272173374, 0.725
+    o, rho0, rv, rl = _drop_state(0.36, a, 96, 24.0, tau)
+    assert 1.1e3 < rl / rv < 1.3e3
+    o.init(rho0)
+    o.step(300)
+    rho = o.moments()[0]
+    assert np.all(np.isfinite(rho)) and rho.min() > 0.5 * rv and rho.max() < 1.05 * rl
+
+    o.init(rho0)
+    F = o.moments()[3]
+    o.init(rho0, F / (2 * np.tile(rho0, 2)))
+    diverged = False
+    for _ in range(15):
+        o.step(20)
+        r = o.moments()[0]
+        if not np.all(np.isfinite(r)) or r.min() <= 0:
+            diverged = True
+            break
+    assert diverged
