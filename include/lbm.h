@@ -187,11 +187,12 @@ int lbm_set_chunk(lbm_handle h, int chunk);
 int lbm_autotune(lbm_handle h, int *chunk_out);
 
 /* ---- Batches: many lattices advanced by one persistent launch ----------
- * A batch holds count >= 1 distinct, initialised handles with LBM_F32
- * storage and the same lattice type, of any sizes and parameters. Each
- * lbm_batch_step launch gives every member one time step (the fused FP32
- * step over all members' tiles, spread over a persistent grid of two CTAs
- * per SM); steps after the first replay a CUDA graph of two launches. Each
+ * A batch holds count >= 1 distinct, initialised handles with the same
+ * storage (LBM_F32, LBM_F16S or LBM_BF16S, not LBM_F64) and the same lattice
+ * type, of any sizes and parameters; otherwise LBM_EINVAL. Each
+ * lbm_batch_step launch gives every member one time step (the fused step of
+ * that storage over all members' tiles, spread over a persistent grid of two
+ * CTAs per SM); steps after the first replay a CUDA graph of two launches. Each
  * member's result is bitwise the same as stepping it alone. While the batch
  * exists the members' work is ordered on the batch's stream (members must
  * not be stepped, initialised or written individually); lbm_batch_destroy

@@ -808,7 +808,7 @@ struct lbm_batch_ctx {
     std::vector<lbm_ctx *> members;
     std::vector<int> cur0;   // each member's buffer index when the batch was made
     std::vector<cudaStream_t> prev;   // each member's stream before the batch
-    int lattice = 0;
+    int lattice = 0, storage = LBM_F32;
     cudaStream_t stream = nullptr;
     lbmf::MemberF *d_members[2] = {nullptr, nullptr};   // step parity 0 and 1
     lbmf::WorkItem *d_items = nullptr;
@@ -819,11 +819,29 @@ struct lbm_batch_ctx {
 
 namespace {
 
+template <int LAT, typename ST>
+void launch_batch_shifted(lbm_batch_ctx *b, int parity, cudaStream_t s)
+{
+    static bool attr_set = false;   // once per kernel instance per process
+    const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
+    if (!attr_set) {
+        cudaFuncSetAttribute(lbmf::k_step_shifted_batch<LAT, ST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        attr_set = true;
+    }
+    lbmf::k_step_shifted_batch<LAT, ST>
+        <<<b->grid, lbmf::LatF<LAT>::TX * lbmf::LatF<LAT>::TY, bytes, s>>>(
+            b->d_members[parity], b->d_items, b->n_items);
+}
+
 template <int LAT>
 void launch_batch(lbm_batch_ctx *b, int parity, cudaStream_t s)
 {
-    lbmf::k_step_f32_batch<LAT><<<b->grid, lbmf::LatF<LAT>::TX * lbmf::LatF<LAT>::TY, 0, s>>>(
-        b->d_members[parity], b->d_items, b->n_items);
+    if (b->storage == LBM_F16S) launch_batch_shifted<LAT, __half>(b, parity, s);
+    else if (b->storage == LBM_BF16S) launch_batch_shifted<LAT, __nv_bfloat16>(b, parity, s);
+    else
+        lbmf::k_step_f32_batch<LAT><<<b->grid, lbmf::LatF<LAT>::TX * lbmf::LatF<LAT>::TY, 0, s>>>(
+            b->d_members[parity], b->d_items, b->n_items);
 }
 
 void batch_launch(lbm_batch_ctx *b, int parity, cudaStream_t s)
@@ -853,9 +871,11 @@ int lbm_batch_create(lbm_batch *out, const lbm_handle *members, int count)
     if (!out || !members || count < 1) return LBM_EINVAL;
     *out = nullptr;
     const int lattice = members[0] ? members[0]->lattice : -1;
+    const int storage = members[0] ? members[0]->storage : -1;
+    if (storage == LBM_F64) return LBM_EINVAL;
     for (int k = 0; k < count; ++k) {
         lbm_ctx *h = members[k];
-        if (!h || !h->initialised || h->bad || h->storage != LBM_F32 || h->lattice != lattice)
+        if (!h || !h->initialised || h->bad || h->storage != storage || h->lattice != lattice)
             return LBM_EINVAL;
         for (int j = 0; j < k; ++j)
             if (members[j] == h) return LBM_EINVAL;   // a lattice at most once
@@ -863,6 +883,7 @@ int lbm_batch_create(lbm_batch *out, const lbm_handle *members, int count)
     lbm_batch_ctx *b = new (std::nothrow) lbm_batch_ctx();
     if (!b) return LBM_ENOMEM;
     b->lattice = lattice;
+    b->storage = storage;
     b->members.assign(members, members + count);
     for (lbm_ctx *h : b->members) {
         b->cur0.push_back(h->cur);
@@ -886,8 +907,10 @@ int lbm_batch_create(lbm_batch *out, const lbm_handle *members, int count)
             m.g = h->geof;
             m.p = h->physf;
             m.mask = h->any_solid ? h->mask : nullptr;
-            m.src = static_cast<const float *>(h->fv[h->cur ^ par]);
-            m.dst = static_cast<float *>(h->fv[h->cur ^ par ^ 1]);
+            m.src = h->fv[h->cur ^ par];
+            m.dst = h->fv[h->cur ^ par ^ 1];
+            m.rho_src = h->rs[h->cur ^ par];
+            m.rho_dst = h->rs[h->cur ^ par ^ 1];
             m.status = h->status;
             m.tiles_x = tx;
             m.tiles_y = ty;

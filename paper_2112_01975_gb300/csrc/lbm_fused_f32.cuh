@@ -442,14 +442,16 @@ k_step_shifted(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
                                             blockIdx.z, sm, rho_src, rho_dst);
 }
 
-// Many lattices of one type in one launch: descriptor of one member for the
-// current step parity, and the (member, tile) work items.
+// Many lattices of one type and one storage in one launch: descriptor of one
+// member for the current step parity, and the (member, tile) work items.
 struct MemberF {
     GeoF g;
     PhysF p;
     const uint8_t *mask;   // nullptr when the member has no solid node
-    const float *src;
-    float *dst;
+    const void *src;       // float, or 16-bit shifted populations
+    void *dst;
+    const float *rho_src;  // shifted storage: densities of src and dst
+    float *rho_dst;
     int *status;
     int tiles_x, tiles_y;
 };
@@ -469,11 +471,32 @@ k_step_f32_batch(const MemberF *__restrict__ members, const WorkItem *__restrict
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         const MemberF &m = members[w.member];
+        const float *src = static_cast<const float *>(m.src);
+        float *dst = static_cast<float *>(m.dst);
         if (m.mask)
-            fused_tile<LAT, true>(m.g, m.p, m.mask, m.src, m.dst, m.status, w.bx, w.by, w.bz, sm);
+            fused_tile<LAT, true>(m.g, m.p, m.mask, src, dst, m.status, w.bx, w.by, w.bz, sm);
         else
-            fused_tile<LAT, false>(m.g, m.p, m.mask, m.src, m.dst, m.status, w.bx, w.by, w.bz, sm);
+            fused_tile<LAT, false>(m.g, m.p, m.mask, src, dst, m.status, w.bx, w.by, w.bz, sm);
         __syncthreads();   // the rings are reused by the next item
+    }
+}
+
+// The same over members with 16-bit shifted storage (no solid nodes);
+// dynamic shared memory of sizeof(SharedS<LAT>).
+template <int LAT, typename ST>
+__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
+k_step_shifted_batch(const MemberF *__restrict__ members, const WorkItem *__restrict__ items,
+                     int n_items)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const MemberF &m = members[w.member];
+        fused_tile<LAT, false, ST, SharedS<LAT>>(m.g, m.p, nullptr, static_cast<const ST *>(m.src),
+                                                static_cast<ST *>(m.dst), m.status, w.bx, w.by,
+                                                w.bz, sm, m.rho_src, m.rho_dst);
+        __syncthreads();
     }
 }
 

@@ -1,11 +1,12 @@
 """Continuous-batching server for parameter-sweep solves.
 
 Requests (a drop on D2Q9 or D3Q27 at some size, T/Tc and radius, a number
-of steps) arrive over time. The server keeps every admitted lattice resident
-on the GPU, admits waiting requests in arrival order as soon as their
-device-memory footprint fits the budget, and advances all resident lattices
-of a lattice type together with one batched launch per step (lbm_batch_*),
-in ticks of a fixed number of steps. A lattice that has finished its steps
+of steps, FP32 or FP16-shifted storage) arrive over time. The server keeps
+every admitted lattice resident on the GPU, admits waiting requests in
+arrival order as soon as their device-memory footprint fits the budget, and
+advances all resident lattices of one lattice type and storage together with
+one batched launch per step (lbm_batch_*), in ticks of a fixed number of
+steps. A lattice that has finished its steps
 is read back and freed at the end of its tick, which frees room for the
 next arrivals. Every step of every solve runs in the library's kernels; a
 member of a batch evolves bitwise as it would alone.
@@ -23,7 +24,7 @@ import time
 import numpy as np
 
 from . import eos_tables, inputs
-from .lbm import D2Q9, D3Q27, F32, F64, LBM, Batch, LBMError
+from .lbm import D2Q9, D3Q27, F16S, F32, F64, LBM, Batch, LBMError
 
 
 @dataclasses.dataclass(frozen=True)
@@ -37,6 +38,7 @@ class Request:
     oscillating: bool     # n = 2 shape mode instead of a round drop
     steps: int
     seed: int
+    storage: int = F32    # storage on the server (F32 or F16S)
 
     @property
     def nodes(self) -> int:
@@ -58,13 +60,14 @@ class Result:
 
 def sweep_requests(count: int = 512, rate: float = 50.0, seed: int = 5, steps: int = 5000,
                    sizes_2d=tuple(range(64, 513, 32)), sizes_3d=tuple(range(64, 193, 32)),
-                   tr=(0.5, 0.95), radius=(0.15, 0.35)) -> list[Request]:
+                   tr=(0.5, 0.95), radius=(0.15, 0.35), storages=(F32, F16S)) -> list[Request]:
     """Poisson arrivals (exponential gaps of mean 1/rate); each request a
     D2Q9 or D3Q27 drop with probability 1/2, size uniform over the given
     sides, T/Tc and radius fraction uniform in their ranges, round or n = 2
-    oscillating with probability 1/2. All draws from splitmix64(seed ^ k)."""
-    u = (inputs.uniform_pm1(seed, 6 * count) + 1.0) / 2.0   # U[0, 1)
-    u = u.reshape(count, 6)
+    oscillating with probability 1/2, storage uniform over the given ones.
+    All draws from splitmix64(seed ^ k)."""
+    u = (inputs.uniform_pm1(seed, 7 * count) + 1.0) / 2.0   # U[0, 1)
+    u = u.reshape(count, 7)
     reqs, t = [], 0.0
     for k in range(count):
         t += -math.log(1.0 - u[k, 0]) / rate
@@ -73,16 +76,15 @@ def sweep_requests(count: int = 512, rate: float = 50.0, seed: int = 5, steps: i
         n = sizes[min(int(u[k, 2] * len(sizes)), len(sizes) - 1)]
         reqs.append(Request(k, t, lat, n, tr[0] + (tr[1] - tr[0]) * u[k, 3],
                             radius[0] + (radius[1] - radius[0]) * u[k, 4], bool(u[k, 5] >= 0.5),
-                            steps, 1000 + k))
+                            steps, 1000 + k,
+                            storages[min(int(u[k, 6] * len(storages)), len(storages) - 1)]))
     return reqs
 
 
-def setup(req: Request):
+def setup(req: Request, width: float = 5.0):
     """EOS parameters and the initial density of a request (van der Waals,
-    attraction scaled for a liquid dP/drho of 0.1; interface width 5 on D2Q9
-    and 7 on D3Q27, where width-5 drops below T/Tc ~ 0.65 diverge in FP64 as
-    well as in FP32)."""
-    width = 7.0 if req.lattice == D3Q27 else 5.0
+    attraction scaled for a liquid dP/drho of 0.1, interface width 5); the
+    lattice starts at rest in the physical velocity (lbm_init)."""
     a = eos_tables.stable_a(0, req.t_over_tc)
     rv, rl, _ = eos_tables.coexistence(0, req.t_over_tc, a)
     kappa = eos_tables.kappa_for_width(0, req.t_over_tc, a, width=width)
@@ -105,9 +107,10 @@ def setup(req: Request):
     return dict(eos=0, t_over_tc=req.t_over_tc, kappa=kappa, tau=tau, a=a), rho
 
 
-def footprint(req: Request, storage: int = F32) -> int:
+def footprint(req: Request, storage: int | None = None) -> int:
     nz = req.n if req.lattice == D3Q27 else 1
-    return LBM.required_bytes(req.lattice, req.n, req.n, nz, storage)
+    return LBM.required_bytes(req.lattice, req.n, req.n, nz,
+                              req.storage if storage is None else storage)
 
 
 def _failed(req: Request, t0: float) -> Result:
@@ -159,7 +162,7 @@ class Server:
                 if used + need > self.hbm_budget:
                     break
                 req = pending.pop(0)
-                active.append([req, _open(req, F32, prepared), req.steps])
+                active.append([req, _open(req, req.storage, prepared), req.steps])
                 used += need
             self.peak_resident = max(self.peak_resident, len(active))
             if not active:
@@ -168,12 +171,11 @@ class Server:
                 continue
             k = min(self.tick_steps, min(a[2] for a in active))
             batches = []
-            for lat in (D2Q9, D3Q27):
-                members = [a[1] for a in active if a[0].lattice == lat]
-                if members:
-                    b = Batch(members)
-                    b.step(k)          # both lattice types' launches overlap on the GPU
-                    batches.append(b)
+            for key in sorted({(a[0].lattice, a[0].storage) for a in active}):
+                members = [a[1] for a in active if (a[0].lattice, a[0].storage) == key]
+                b = Batch(members)
+                b.step(k)              # the groups' launches overlap on the GPU
+                batches.append(b)
             for b in batches:
                 try:
                     b.sync()

@@ -1,5 +1,5 @@
-"""Batches: many FP32 lattices of different sizes and parameters advanced by
-one persistent launch per step. Each member must come out bitwise equal to
+"""Batches: many FP32 (or FP16/BF16-shifted) lattices of different sizes and
+parameters advanced by one persistent launch per step. Each member must come out bitwise equal to
 the same lattice stepped alone (the per-tile arithmetic is the same code and
 no data crosses members)."""
 import numpy as np
@@ -36,9 +36,9 @@ def d3q27_members(L):
     return out
 
 
-def make(L, spec):
+def make(L, spec, storage=None):
     args, kw, rho = spec
-    g = L.LBM(*args, storage=L.F32, **kw)
+    g = L.LBM(*args, storage=L.F32 if storage is None else storage, **kw)
     g.init(rho)
     return g
 
@@ -98,3 +98,41 @@ def test_batch_rejects_mixed_members(lbm):
         lbm.Batch([a, c])          # FP64 member
     with pytest.raises(lbm.LBMError):
         lbm.Batch([a, a])          # the same lattice twice
+
+
+@pytest.mark.parametrize("storage", [2, 3])
+def test_shifted_batch_equals_alone(lbm, storage):
+    """FP16- and BF16-shifted members (no solids: shifted storage takes none)
+    of both lattice types, each batch bitwise equal to its members alone."""
+    w2, w3 = inputs.DROP_D2Q9_64, inputs.DROP_D3Q27_128
+    specs = {0: [], 1: []}
+    for k, (nx, ny) in enumerate([(64, 64), (96, 40), (37, 29)]):
+        rho = inputs.add_noise(inputs.drop(nx, ny, 1, min(nx, ny) / 4, w2.rho_v, w2.rho_l), 1e-4, 50 + k)
+        specs[0].append(((0, nx, ny, 1, w2.eos, w2.t_over_tc, w2.kappa, 0.9), dict(a=w2.a, b=w2.b), rho))
+    for k, (nx, ny, nz) in enumerate([(40, 36, 33), (32, 32, 32)]):
+        rho = inputs.add_noise(inputs.drop(nx, ny, nz, min(nx, ny, nz) / 4, w3.rho_v, w3.rho_l), 1e-4, 60 + k)
+        specs[1].append(((1, nx, ny, nz, w3.eos, w3.t_over_tc, w3.kappa, 0.8), dict(a=w3.a, b=w3.b), rho))
+    for lat in (0, 1):
+        alone = []
+        for sp in specs[lat]:
+            g = make(lbm, sp, storage)
+            g.step(13)
+            alone.append(g.get_populations())
+        members = [make(lbm, sp, storage) for sp in specs[lat]]
+        b = lbm.Batch(members)
+        b.step(13)
+        b.sync()
+        assert b.launches == 13
+        for g, ref in zip(members, alone):
+            assert np.array_equal(g.get_populations(), ref)
+        b.close()
+
+
+def test_batch_rejects_mixed_storage(lbm):
+    w = inputs.DROP_D2Q9_64
+    a = lbm.LBM(0, 32, 32, 1, w.eos, w.t_over_tc, w.kappa, 1.0, a=w.a, b=w.b, storage=lbm.F32)
+    c = lbm.LBM(0, 32, 32, 1, w.eos, w.t_over_tc, w.kappa, 1.0, a=w.a, b=w.b, storage=lbm.F16S)
+    a.init(np.full(1024, 2.0))
+    c.init(np.full(1024, 2.0))
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([a, c])

@@ -22,6 +22,8 @@ def test_sweep_requests_deterministic_and_in_range():
         assert (64 <= r.n <= 192) if r.lattice == 1 else (64 <= r.n <= 512)
     frac3d = np.mean([r.lattice == 1 for r in a])
     assert 0.35 < frac3d < 0.65
+    assert {r.storage for r in a} == {1, 2}                # FP32 and FP16-shifted
+    assert 0.35 < np.mean([r.storage == 2 for r in a]) < 0.65
 
 
 @pytest.mark.parametrize("eos,tr", [(0, 0.5), (0, 0.8), (0, 0.95), (1, 0.7)])
