@@ -58,8 +58,16 @@ typedef struct lbm_ctx *lbm_handle;
 enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q27 = 1 };
 
 /* Equations of state of Sec. 3.1: van der Waals (Eq. vdWEoS), Peng-Robinson
- * (Eq. PREoS), Redlich-Kwong-Soave (Eq. RKSEoS), Carnahan-Starling (Eq. CSEos). */
-enum lbm_eos { LBM_EOS_VDW = 0, LBM_EOS_PR = 1, LBM_EOS_RKS = 2, LBM_EOS_CS = 3 };
+ * (Eq. PREoS), Redlich-Kwong-Soave (Eq. RKSEoS), Carnahan-Starling (Eq. CSEos);
+ * and the two Shan-Chen forms of Appendix C, P = rho/3 + (G/6) psi_SC^2 with
+ * psi_SC = 1 - exp(-rho) (Eq. SC1, critical coupling G_c = -4) or
+ * exp(-1/rho) (Eq. SC2, G_c = -e^2). For these T/Tc sets the coupling
+ * G = G_c / (T/Tc), and the a, b of lbm_params are not used (b must still
+ * be positive). */
+enum lbm_eos {
+    LBM_EOS_VDW = 0, LBM_EOS_PR = 1, LBM_EOS_RKS = 2, LBM_EOS_CS = 3,
+    LBM_EOS_SC1 = 4, LBM_EOS_SC2 = 5
+};
 
 /* Population storage. LBM_F64 stores and computes in FP64 (two kernels per
  * step). LBM_F32 stores populations in FP32 and runs the step as one fused

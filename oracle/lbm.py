@@ -17,13 +17,16 @@ PHI_OFF = 2
 FORCE_PRINTED_SIGN = 4
 PHI_PRINTED_SIGN = 8
 
-EOS_VDW, EOS_PR, EOS_RKS, EOS_CS = 0, 1, 2, 3
+EOS_VDW, EOS_PR, EOS_RKS, EOS_CS, EOS_SC1, EOS_SC2 = 0, 1, 2, 3, 4, 5
 
 # Default EOS constants (lattice units): van der Waals a = 9/49, b = 2/21;
 # Peng-Robinson and Redlich-Kwong-Soave a = 2/49, b = 2/21, acentric 0.344
-# (the paper's water value, Sec. 3.1); Carnahan-Starling a = 1, b = 4.
+# (the paper's water value, Sec. 3.1); Carnahan-Starling a = 1, b = 4. The
+# Shan-Chen forms (Appendix C) take no a, b: their b here only bounds the
+# density range the Maxwell tools search (rho < 1/b).
 DEFAULT_AB = {EOS_VDW: (9.0 / 49.0, 2.0 / 21.0), EOS_PR: (2.0 / 49.0, 2.0 / 21.0),
-              EOS_RKS: (2.0 / 49.0, 2.0 / 21.0), EOS_CS: (1.0, 4.0)}
+              EOS_RKS: (2.0 / 49.0, 2.0 / 21.0), EOS_CS: (1.0, 4.0),
+              EOS_SC1: (1.0, 0.1), EOS_SC2: (1.0, 0.1)}
 DEFAULT_ACENTRIC = 0.344
 
 _lib = None
@@ -59,6 +62,8 @@ def lib():
                                           C.c_double, C.c_double]
         L.oracle_eos_RTc.restype = C.c_double
         L.oracle_eos_RTc.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.oracle_eos_temperature.restype = C.c_double
+        L.oracle_eos_temperature.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
         L.oracle_eos_alpha.restype = C.c_double
         L.oracle_eos_alpha.argtypes = [C.c_int, C.c_double, C.c_double]
         L.oracle_eos_pressure_array.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
@@ -85,7 +90,7 @@ class EOS:
         self.t_over_tc = t_over_tc
         L = lib()
         self.RTc = L.oracle_eos_RTc(eos, self.a, self.b)
-        self.RT = t_over_tc * self.RTc
+        self.RT = L.oracle_eos_temperature(eos, self.a, self.b, t_over_tc)
         self.alpha = L.oracle_eos_alpha(eos, acentric, t_over_tc)
 
     def __call__(self, rho):

@@ -9,7 +9,8 @@
  * It follows the paper's steps in the paper's order, with naive loops over
  * all Q directions and no blocking, fusion or reordering:
  *   moments            Sec. 2.3.3, rho = sum f_i, rho u = sum c_i f_i
- *   equation of state  Sec. 3.1, Eqs. vdWEoS, PREoS, RKSEoS, CSEos
+ *   equation of state  Sec. 3.1, Eqs. vdWEoS, PREoS, RKSEoS, CSEos; Appendix C,
+ *                      Eqs. SCeos, SC1, SC2 (Shan-Chen)
  *   pseudo-potential   Sec. 2.3.4, psi = sqrt|P - P0|, P0 = rho/3 (end of Sec. 2.3.5)
  *   Korteweg force     Eq. Kforce_final with w_i of Eq. wi
  *   correction Phi     Eq. correction, central difference along alpha
@@ -102,6 +103,14 @@ double oracle_eos_pressure(int eos, double a, double b, double RT, double alpha,
         return rho * RT * (1.0 + e + e * e - e * e * e) / ((1.0 - e) * (1.0 - e) * (1.0 - e))
                - a * rho * rho;
     }
+    case 4: { /* Shan-Chen, Eqs. SCeos and SC1; RT holds the coupling G */
+        double psi = 1.0 - exp(-rho);
+        return rho / 3.0 + RT / 6.0 * psi * psi;
+    }
+    case 5: { /* Shan-Chen, Eqs. SCeos and SC2; RT holds the coupling G */
+        double psi = exp(-1.0 / rho);
+        return rho / 3.0 + RT / 6.0 * psi * psi;
+    }
     }
     return NAN;
 }
@@ -114,8 +123,19 @@ double oracle_eos_RTc(int eos, double a, double b)
     case 1: return (0.0778 / 0.45724) * a / b;
     case 2: return (0.08664 / 0.42748) * a / b;
     case 3: return (0.18727 / 0.4963) * a / b;
+    case 4: return -4.0;              /* critical coupling G_c of Eq. SC1 (Appendix C) */
+    case 5: return -exp(2.0);         /* critical coupling G_c of Eq. SC2 */
     }
     return NAN;
+}
+
+/* The temperature parameter of each EOS at T/Tc: R T = (T/Tc) R Tc for the
+ * cubic equations; for Shan-Chen the coupling G = G_c / (T/Tc) (G plays the
+ * role of an inverse temperature: |G| > |G_c| separates phases). */
+double oracle_eos_temperature(int eos, double a, double b, double t_over_tc)
+{
+    double c = oracle_eos_RTc(eos, a, b);
+    return eos >= 4 ? c / t_over_tc : t_over_tc * c;
 }
 
 /* alpha(T) of PR and RKS, Sec. 3.1; 1 for vdW and CS. */
@@ -161,7 +181,7 @@ oracle_ctx *oracle_create(int lattice, int nx, int ny, int nz, int eos, double t
     o->eos = eos;
     o->a = a; o->b = b; o->acentric = acentric;
     o->RTc = oracle_eos_RTc(eos, a, b);
-    o->RT = t_over_tc * o->RTc;
+    o->RT = oracle_eos_temperature(eos, a, b, t_over_tc);
     o->alpha = oracle_eos_alpha(eos, acentric, t_over_tc);
     o->kappa = kappa;
     o->omega = 1.0 / tau;

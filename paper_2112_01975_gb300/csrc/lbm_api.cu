@@ -128,8 +128,18 @@ double eos_rtc(int eos, double a, double b)
     case LBM_EOS_PR: return (0.0778 / 0.45724) * a / b;
     case LBM_EOS_RKS: return (0.08664 / 0.42748) * a / b;
     case LBM_EOS_CS: return (0.18727 / 0.4963) * a / b;
+    case LBM_EOS_SC1: return -4.0;          // critical coupling G_c (Appendix C)
+    case LBM_EOS_SC2: return -std::exp(2.0);
     }
     return NAN;
+}
+
+// The EOS's temperature parameter at T/Tc: R T for the cubic equations, the
+// coupling G = G_c / (T/Tc) for Shan-Chen (kept in the RT slot).
+double eos_temperature(int eos, double a, double b, double tr)
+{
+    const double c = eos_rtc(eos, a, b);
+    return eos >= LBM_EOS_SC1 ? c / tr : tr * c;
 }
 
 double eos_alpha(int eos, double acentric, double tr)
@@ -477,6 +487,8 @@ int lbm_default_params(int eos, lbm_params *p)
     case LBM_EOS_PR:
     case LBM_EOS_RKS: p->a = 2.0 / 49.0; p->b = 2.0 / 21.0; break;
     case LBM_EOS_CS: p->a = 1.0; p->b = 4.0; break;
+    case LBM_EOS_SC1:
+    case LBM_EOS_SC2: p->a = 1.0; p->b = 1.0; break;   // not used by Shan-Chen
     default: return LBM_EINVAL;
     }
     p->acentric = 0.344;
@@ -499,7 +511,7 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     if (!out) return LBM_EINVAL;
     *out = nullptr;
     if (!valid_shape(lattice, nx, ny, nz)) return LBM_EINVAL;
-    if (eos < LBM_EOS_VDW || eos > LBM_EOS_CS) return LBM_EINVAL;
+    if (eos < LBM_EOS_VDW || eos > LBM_EOS_SC2) return LBM_EINVAL;
     if (!(t_over_tc > 0.0 && t_over_tc < 1.0) || !(kappa >= 0.0) || !(tau > 0.5)) return LBM_EINVAL;
     lbm_params prm;
     if (p) prm = *p;
@@ -524,7 +536,7 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     ph.eos = eos;
     ph.a = prm.a;
     ph.b = prm.b;
-    ph.RT = t_over_tc * eos_rtc(eos, prm.a, prm.b);
+    ph.RT = eos_temperature(eos, prm.a, prm.b, t_over_tc);
     ph.alpha = eos_alpha(eos, prm.acentric, t_over_tc);
     ph.kappa = kappa;
     ph.omega = 1.0 / tau;
@@ -556,6 +568,16 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
         case LBM_EOS_VDW: P = rep - pf.a * r * r; break;
         case LBM_EOS_PR: P = rep - pf.aalpha * r * r / (1.0f + 2.0f * pf.b * r - pf.b * pf.b * r * r); break;
         case LBM_EOS_RKS: P = rep - pf.aalpha * r * r / (1.0f + pf.b * r); break;
+        case LBM_EOS_SC1: {
+            const float q = 1.0f - std::exp(-r);
+            P = r * (1.0f / 3.0f) + pf.RT / 6.0f * q * q;
+            break;
+        }
+        case LBM_EOS_SC2: {
+            const float q = std::exp(-1.0f / r);
+            P = r * (1.0f / 3.0f) + pf.RT / 6.0f * q * q;
+            break;
+        }
         default: {
             const float e = 0.25f * pf.b * r, om = 1.0f - e;
             P = r * pf.RT * (1.0f + e + e * e - e * e * e) / (om * om * om) - pf.a * r * r;

@@ -72,25 +72,40 @@ template <int LAT> __device__ __forceinline__ constexpr float weight_f(int i)
            (L::cz(i) ? 1.0f / 6.0f : 2.0f / 3.0f);
 }
 
-// P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 equations of state).
+// P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 and Appendix C equations of state).
+// Every operation is an explicitly rounded intrinsic, so each inlined call
+// site rounds the same way (no call-site-dependent contraction).
 __device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
 {
-    const float br = p.b * rho, r3 = rho * (1.0f / 3.0f);
+    const float br = __fmul_rn(p.b, rho), rr = __fmul_rn(rho, rho);
+    const float nr3 = __fmul_rn(rho, -1.0f / 3.0f);
+    const float rt = __fmul_rn(rho, p.RT);
     switch (p.eos) {
-    case 0:
-        return rho * p.RT * __frcp_rn(1.0f - br) - p.a * rho * rho - r3;
-    case 1: {
-        const float d1 = 1.0f - br, d2 = 1.0f + 2.0f * br - br * br;
-        return (rho * p.RT * d2 - p.aalpha * rho * rho * d1) * __frcp_rn(d1 * d2) - r3;
+    case 0:   // rho RT / (1 - b rho) - a rho^2 - rho/3
+        return __fmaf_rn(-p.a, rr, __fmaf_rn(rt, __frcp_rn(__fsub_rn(1.0f, br)), nr3));
+    case 1: {   // PR: d1 = 1 - b rho, d2 = 1 + 2 b rho - (b rho)^2
+        const float d1 = __fsub_rn(1.0f, br), d2 = __fmaf_rn(br, __fsub_rn(2.0f, br), 1.0f);
+        const float num = __fmaf_rn(rt, d2, -__fmul_rn(__fmul_rn(p.aalpha, rr), d1));
+        return __fmaf_rn(num, __frcp_rn(__fmul_rn(d1, d2)), nr3);
     }
-    case 2: {
-        const float d1 = 1.0f - br, d2 = 1.0f + br;
-        return (rho * p.RT * d2 - p.aalpha * rho * rho * d1) * __frcp_rn(d1 * d2) - r3;
+    case 2: {   // RKS: d1 = 1 - b rho, d2 = 1 + b rho
+        const float d1 = __fsub_rn(1.0f, br), d2 = __fadd_rn(1.0f, br);
+        const float num = __fmaf_rn(rt, d2, -__fmul_rn(__fmul_rn(p.aalpha, rr), d1));
+        return __fmaf_rn(num, __frcp_rn(__fmul_rn(d1, d2)), nr3);
     }
-    default: {
-        const float e = 0.25f * br, om = 1.0f - e;
-        return rho * p.RT * (1.0f + e + e * e - e * e * e) * __frcp_rn(om * om * om) -
-               p.a * rho * rho - r3;
+    case 4: {   // Shan-Chen, psi_SC = 1 - exp(-rho): P - rho/3 = (G/6) psi_SC^2, G in RT
+        const float q = __fsub_rn(1.0f, expf(-rho));
+        return __fmul_rn(__fmul_rn(q, q), __fmul_rn(p.RT, 1.0f / 6.0f));
+    }
+    case 5: {   // Shan-Chen, psi_SC = exp(-1/rho)
+        const float q = expf(-__frcp_rn(rho));
+        return __fmul_rn(__fmul_rn(q, q), __fmul_rn(p.RT, 1.0f / 6.0f));
+    }
+    default: {   // CS with e = b rho / 4
+        const float e = __fmul_rn(0.25f, br), om = __fsub_rn(1.0f, e);
+        const float poly = __fmaf_rn(__fmul_rn(e, e), __fsub_rn(1.0f, e), __fadd_rn(1.0f, e));
+        const float den = __fmul_rn(__fmul_rn(om, om), om);
+        return __fmaf_rn(-p.a, rr, __fmaf_rn(__fmul_rn(rt, poly), __frcp_rn(den), nr3));
     }
     }
 }

@@ -35,7 +35,7 @@ __host__ __device__ constexpr int cxi(int i) { return i % 3 - 1; }
 __host__ __device__ constexpr int cyi(int i) { return (i / 3) % 3 - 1; }
 __host__ __device__ constexpr int czi(int i) { return i / 9 - 1; }
 
-// Pressure of the equations of state of Sec. 3.1 (gas constant 1).
+// Pressure of the equations of state of Sec. 3.1 and Appendix C (gas constant 1).
 __device__ __forceinline__ double eos_pressure(const Phys &p, double rho)
 {
     switch (p.eos) {
@@ -49,10 +49,18 @@ __device__ __forceinline__ double eos_pressure(const Phys &p, double rho)
         const double d1 = 1.0 - p.b * rho, d2 = 1.0 + p.b * rho;
         return (rho * p.RT * d2 - p.a * p.alpha * rho * rho * d1) / (d1 * d2);
     }
-    default: {  // Carnahan-Starling
+    case 3: {  // Carnahan-Starling
         const double e = 0.25 * p.b * rho;
         const double om = 1.0 - e;
         return rho * p.RT * (1.0 + e + e * e - e * e * e) / (om * om * om) - p.a * rho * rho;
+    }
+    case 4: {  // Shan-Chen, psi_SC = 1 - exp(-rho); RT holds the coupling G
+        const double q = 1.0 - exp(-rho);
+        return rho * (1.0 / 3.0) + p.RT * (1.0 / 6.0) * q * q;
+    }
+    default: {  // Shan-Chen, psi_SC = exp(-1/rho)
+        const double q = exp(-1.0 / rho);
+        return rho * (1.0 / 3.0) + p.RT * (1.0 / 6.0) * q * q;
     }
     }
 }

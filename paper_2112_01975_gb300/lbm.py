@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 
 D2Q9, D3Q27 = 0, 1
-EOS_VDW, EOS_PR, EOS_RKS, EOS_CS = 0, 1, 2, 3
+EOS_VDW, EOS_PR, EOS_RKS, EOS_CS, EOS_SC1, EOS_SC2 = 0, 1, 2, 3, 4, 5
 F64, F32, F16S, BF16S = 0, 1, 2, 3
 FLAG_PHI_OFF = 1
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",

@@ -62,13 +62,14 @@ def test_default_params(lib):
     assert p.a == pytest.approx(9 / 49) and p.b == pytest.approx(2 / 21)
     assert lib.lbm_default_params(1, C.byref(p)) == 0
     assert p.a == pytest.approx(2 / 49) and p.acentric == pytest.approx(0.344)
+    assert lib.lbm_default_params(4, C.byref(p)) == 0 and p.b > 0    # Shan-Chen: a, b unused
     assert lib.lbm_default_params(9, C.byref(p)) == 1
 
 
 @pytest.mark.parametrize("args", [
     (0, 64, 64, 2, 0, 0.8, 0.02, 1.0),     # D2Q9 with nz != 1
     (1, 64, 64, 4, 0, 0.8, 0.02, 1.0),     # nz < 5
-    (1, 64, 64, 64, 5, 0.8, 0.02, 1.0),    # unknown EOS
+    (1, 64, 64, 64, 6, 0.8, 0.02, 1.0),    # unknown EOS
     (1, 64, 64, 64, 0, 1.2, 0.02, 1.0),    # T/Tc >= 1
     (1, 64, 64, 64, 0, 0.8, -0.1, 1.0),    # kappa < 0
     (1, 64, 64, 64, 0, 0.8, 0.02, 0.5),    # tau <= 1/2

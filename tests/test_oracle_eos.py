@@ -1,7 +1,7 @@
 """Pins of the oracle's equations of state and of the host-side closed forms.
 
 Critical points and critical compressibilities are textbook values of each
-EOS (Sec. 3.1); the van der Waals Maxwell construction is checked with the
+EOS (Sec. 3.1), and for the Shan-Chen forms the values Appendix C prints; the van der Waals Maxwell construction is checked with the
 closed-form antiderivative of P/rho^2, not with the quadrature the tool uses.
 """
 import math
@@ -45,6 +45,37 @@ def test_critical_compressibility(eos, zc):
     scale = e(rc) / rc
     assert abs(d1) < 2e-3 * scale
     assert e(rc) / (rc * e.RTc) == pytest.approx(zc, rel=2e-3)
+
+
+@pytest.mark.parametrize("eos,gc,rc", [(4, -4.0, math.log(2.0)), (5, -math.exp(2.0), 1.0)])
+def test_shan_chen_critical_points(eos, gc, rc):
+    """The critical couplings and densities the paper prints for the two
+    Shan-Chen pseudo-potentials (Appendix C: G_c = -4, rho_c = 0.6931 and
+    G_c = -7.389, rho_c = 1): at T/Tc = 1 the coupling is G_c and P' = P'' = 0
+    at rho_c, and nowhere else does P' vanish."""
+    e = EOS(eos, 1.0)
+    assert e.RT == pytest.approx(gc, rel=1e-15)
+    assert round(rc, 4) == pytest.approx({4: 0.6931, 5: 1.0}[eos], abs=1e-12)
+    assert round(-gc, 3) == pytest.approx({4: 4.0, 5: 7.389}[eos], abs=1e-12)
+    d1, d2 = _d(e, rc)
+    assert abs(d1) < 1e-7 and abs(d2) < 1e-5
+    grid = np.linspace(0.05, 5.0, 4001)
+    assert np.all(np.gradient(e(grid), grid) > -1e-6)          # no loop at T = Tc
+    below = EOS(eos, 0.9)
+    assert np.min(np.gradient(below(grid), grid)) < 0.0          # a van der Waals loop below
+
+
+@pytest.mark.parametrize("eos", [4, 5])
+def test_shan_chen_sound_faster_in_vapour(eos):
+    """The paper's remark on the Shan-Chen forms (Appendix C): at coexistence
+    the isothermal sound speed dP/drho is larger in the vapour than in the
+    liquid, the reverse of the cubic equations of state."""
+    e = EOS(eos, 0.8)
+    rv, rl, _ = ph.maxwell(e)
+    assert _d(e, rv)[0] > _d(e, rl)[0] > 0.0
+    v = EOS(0, 0.8)
+    vv, vl, _ = ph.maxwell(v)
+    assert _d(v, vv)[0] < _d(v, vl)[0]
 
 
 def test_maxwell_vdw_closed_form_area():
