@@ -100,11 +100,16 @@ typedef struct {
     double a, b, acentric, rho_w;
     int storage;   /* enum lbm_storage */
     int flags;     /* LBM_FLAG_* */
+    double g[3];   /* body acceleration (gx, gy, gz; D2Q9 uses gx, gy): the force
+                      rho g joins the Korteweg force in xi* and in U (the generic
+                      force F of Eq. LBGK; Sec. 4.1 drives layered Poiseuille
+                      flow with it). Must be finite; default 0. */
 } lbm_params;
 
 /* Fill p with the defaults of an EOS: vdW a = 9/49, b = 2/21; PR and RKS
- * a = 2/49, b = 2/21; CS a = 1, b = 4; acentric 0.344; rho_w = 1;
- * LBM_F64; no flags. Returns LBM_EINVAL for an unknown eos. */
+ * a = 2/49, b = 2/21; CS a = 1, b = 4; Shan-Chen a = b = 1 (unused);
+ * acentric 0.344; rho_w = 1; LBM_F64; no flags; g = 0. Returns LBM_EINVAL
+ * for an unknown eos. */
 int lbm_default_params(int eos, lbm_params *p);
 
 /* Create a handle for one lattice. lattice: enum lbm_lattice. nx, ny, nz:

@@ -40,7 +40,8 @@ def lib():
         L.oracle_create.restype = C.c_void_p
         L.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                     C.c_double, C.c_double, C.c_void_p, C.c_double,
-                                    C.c_double, C.c_double, C.c_double, C.c_int]
+                                    C.c_double, C.c_double, C.c_double, C.c_int,
+                                    C.c_double, C.c_double, C.c_double]
         L.oracle_destroy.argtypes = [C.c_void_p]
         L.oracle_init.argtypes = [C.c_void_p, _dp, _dp]
         L.oracle_step.argtypes = [C.c_void_p, C.c_long]
@@ -107,7 +108,10 @@ class OracleLBM:
     def __init__(self, lattice: int, nx: int, ny: int, nz: int, eos: int, t_over_tc: float,
                  kappa: float, tau: float, mask: np.ndarray | None = None,
                  a: float | None = None, b: float | None = None,
-                 acentric: float = DEFAULT_ACENTRIC, rho_w: float = 1.0, flags: int = 0):
+                 acentric: float = DEFAULT_ACENTRIC, rho_w: float = 1.0, flags: int = 0,
+                 g=(0.0, 0.0, 0.0)):
+        """g: body acceleration (gx, gy[, gz]); the force rho g is added to the
+        Korteweg force (the generic F of Eq. LBGK)."""
         self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
         self.D = 2 if lattice == 0 else 3
         self.Q = 9 if lattice == 0 else 27
@@ -121,8 +125,9 @@ class OracleLBM:
             self._mask = np.ascontiguousarray(mask, dtype=np.uint8)
             assert self._mask.size == self.N
             mp = self._mask.ctypes.data_as(C.c_void_p)
+        gg = tuple(g) + (0.0,) * (3 - len(g))
         self._h = lib().oracle_create(lattice, nx, ny, nz, eos, t_over_tc, kappa, tau, mp,
-                                      a, b, acentric, rho_w, flags)
+                                      a, b, acentric, rho_w, flags, *map(float, gg))
         if not self._h:
             raise ValueError("oracle_create rejected the arguments")
 

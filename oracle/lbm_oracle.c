@@ -12,7 +12,8 @@
  *   equation of state  Sec. 3.1, Eqs. vdWEoS, PREoS, RKSEoS, CSEos; Appendix C,
  *                      Eqs. SCeos, SC1, SC2 (Shan-Chen)
  *   pseudo-potential   Sec. 2.3.4, psi = sqrt|P - P0|, P0 = rho/3 (end of Sec. 2.3.5)
- *   Korteweg force     Eq. Kforce_final with w_i of Eq. wi
+ *   Korteweg force     Eq. Kforce_final with w_i of Eq. wi, plus an optional
+ *                      body force rho g (the generic F of Eq. LBGK; Sec. 4.1)
  *   correction Phi     Eq. correction, central difference along alpha
  *   collision          Eqs. LBMeq, LBGK, xistar, zetastar, LBMstar
  *   streaming          left side of Eq. LBGK, halfway bounce-back at solids
@@ -72,6 +73,7 @@ typedef struct {
     int eos;
     double a, b, acentric, RTc, RT, alpha;
     double kappa, omega, rho_w;
+    double g[3];      /* body acceleration: force rho g added to F (Sec. 4.1) */
     int flags;
     unsigned char *mask;
     double *f, *fnew;
@@ -158,7 +160,8 @@ static long node_at(const oracle_ctx *o, long x, long y, long z)
 
 oracle_ctx *oracle_create(int lattice, int nx, int ny, int nz, int eos, double t_over_tc,
                           double kappa, double tau, const unsigned char *mask,
-                          double a, double b, double acentric, double rho_w, int flags)
+                          double a, double b, double acentric, double rho_w, int flags,
+                          double gx, double gy, double gz)
 {
     if (lattice != 0 && lattice != 1) return NULL;
     if (lattice == 0 && nz != 1) return NULL;
@@ -187,6 +190,9 @@ oracle_ctx *oracle_create(int lattice, int nx, int ny, int nz, int eos, double t
     o->omega = 1.0 / tau;
     o->rho_w = rho_w;
     o->flags = flags;
+    o->g[0] = gx;
+    o->g[1] = gy;
+    o->g[2] = lattice == 1 ? gz : 0.0;
     long N = o->N;
     o->mask = (unsigned char *)calloc(N, 1);
     if (mask) memcpy(o->mask, mask, N);
@@ -284,7 +290,8 @@ static void force_from_density(oracle_ctx *o)
         for (int al = 0; al < 3; ++al) {
             long k = al * N + n;
             if (o->mask[n] || al >= D) { o->F[k] = 0.0; continue; }
-            o->F[k] = fs * (o->sgn[n] * 2.0 * o->psi[n] * Spsi[k] + o->kappa * o->rho[n] * Srho[k]);
+            o->F[k] = fs * (o->sgn[n] * 2.0 * o->psi[n] * Spsi[k] + o->kappa * o->rho[n] * Srho[k])
+                      + o->rho[n] * o->g[al];
         }
     free(Spsi);
     free(Srho);
@@ -512,7 +519,8 @@ void oracle_post_local(const oracle_ctx *o, const double *block, const unsigned 
     double pref = (o->flags & ORACLE_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * o->omega);
     if (o->flags & ORACLE_PHI_PRINTED_SIGN) pref = -pref;
     for (int al = 0; al < D; ++al) {
-        F[al] = fs * (sgn[c0] * 2.0 * psi[c0] * Spsi[al] + o->kappa * rho[c0] * Srho[al]);
+        F[al] = fs * (sgn[c0] * 2.0 * psi[c0] * Spsi[al] + o->kappa * rho[c0] * Srho[al])
+                + rho[c0] * o->g[al];
         int e[3] = {0, 0, 0};
         e[al] = 1;
         int kp = LIDX(e[0], e[1], e[2]), km = LIDX(-e[0], -e[1], -e[2]);

@@ -121,3 +121,63 @@ def equimolar_radius(rho: np.ndarray, rho_v: float, rho_l: float, dim: int) -> f
     if dim == 2:
         return math.sqrt(excess / math.pi)
     return (3.0 * excess / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def layered_poiseuille(layers, g: float, top: str = "wall"):
+    """Steady body-force-driven flow through flat layers (Sec. 4.1, Eqs.
+    poiseuille_odes and poiseuille_odes_BD): in each layer
+    d/dy(mu du/dy) + rho g = 0, u = 0 at y = 0, u and mu du/dy continuous at
+    each interface, and at the top y = H either u = 0 (top="wall") or
+    du/dy = 0 (top="symmetry", the mid-plane of a channel mirrored about it).
+    layers: [(thickness, rho, mu), ...] from y = 0 upward. Returns u(y).
+    Each layer's u is a parabola a y^2 + B y + C with a = -rho g / (2 mu);
+    the 2K unknowns (B, C) solve the 2K conditions above."""
+    K = len(layers)
+    edges = np.concatenate([[0.0], np.cumsum([t for t, _, _ in layers])])
+    a = [-r * g / (2.0 * m) for _, r, m in layers]
+    A = np.zeros((2 * K, 2 * K))
+    rhs = np.zeros(2 * K)
+    A[0, 1] = 1.0                                        # u(0) = 0
+    row = 1
+    for k in range(K - 1):
+        y = edges[k + 1]
+        mk, mn = layers[k][2], layers[k + 1][2]
+        A[row, 2 * k], A[row, 2 * k + 1] = y, 1.0        # u continuous
+        A[row, 2 * k + 2], A[row, 2 * k + 3] = -y, -1.0
+        rhs[row] = (a[k + 1] - a[k]) * y * y
+        row += 1
+        A[row, 2 * k], A[row, 2 * k + 2] = mk, -mn       # mu du/dy continuous
+        rhs[row] = 2.0 * y * (mn * a[k + 1] - mk * a[k])
+        row += 1
+    H = edges[-1]
+    if top == "wall":
+        A[row, 2 * K - 2], A[row, 2 * K - 1] = H, 1.0
+        rhs[row] = -a[-1] * H * H
+    else:
+        A[row, 2 * K - 2] = 1.0
+        rhs[row] = -2.0 * a[-1] * H
+    BC = np.linalg.solve(A, rhs)
+
+    def u(y):
+        y = np.asarray(y, dtype=float)
+        k = np.clip(np.searchsorted(edges, y, side="right") - 1, 0, K - 1)
+        return np.asarray(a)[k] * y * y + BC[2 * k] * y + BC[2 * k + 1]
+    return u
+
+
+def channel_flow_from_profile(rho_rows, g: float, nu: float):
+    """Steady U(y) of body-force-driven flow along a channel mirrored about
+    its mid-plane, for a density profile across it (rho at the fluid rows,
+    halfway walls half a row beyond the first and last): the momentum
+    balance d/dy(rho nu dU/dy) + rho g = 0 of a parallel flow, integrated
+    row by row. A flat interface adds no shear stress (the Korteweg tensor
+    has no xy part when rho varies along y only), so this is the diffuse-
+    interface counterpart of layered_poiseuille. Even row count assumed."""
+    r = np.asarray(rho_rows, dtype=float)
+    m = len(r) // 2
+    U = np.zeros(len(r))
+    U[0] = 0.5 * g * np.sum(r[:m]) / (nu * r[0])          # wall to the first row
+    for j in range(1, m):
+        U[j] = U[j - 1] + g * np.sum(r[j:m]) / (nu * 0.5 * (r[j - 1] + r[j]))
+    U[m:] = U[:m][::-1]
+    return U

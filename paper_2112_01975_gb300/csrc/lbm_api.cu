@@ -493,6 +493,7 @@ int lbm_default_params(int eos, lbm_params *p)
     }
     p->acentric = 0.344;
     p->rho_w = 1.0;
+    p->g[0] = p->g[1] = p->g[2] = 0.0;
     p->storage = LBM_F64;
     p->flags = 0;
     return LBM_OK;
@@ -521,6 +522,8 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
         for (size_t n = 0; n < (size_t)nx * ny * nz; ++n)
             if (solid_mask[n]) return LBM_EINVAL;   // shifted storage: lattices without solids
     if (!(prm.a > 0.0) || !(prm.b > 0.0) || !(prm.rho_w > 0.0)) return LBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(prm.g[a])) return LBM_EINVAL;
     lbm_ctx *h = new (std::nothrow) lbm_ctx();
     if (!h) return LBM_ENOMEM;
     h->lattice = lattice;
@@ -542,6 +545,7 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     ph.omega = 1.0 / tau;
     ph.phi_pref = (prm.flags & LBM_FLAG_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * ph.omega);
     ph.rho_w = prm.rho_w;
+    for (int a = 0; a < 3; ++a) ph.g[a] = (a < (lattice == LBM_D2Q9 ? 2 : 3)) ? prm.g[a] : 0.0;
     // FP32 fused step: D2Q9 runs in the 3D frame with one y row.
     h->geof.nx = nx;
     h->geof.ny = lattice == LBM_D2Q9 ? 1 : ny;
@@ -559,6 +563,9 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     pf.omw = (float)(1.0 - ph.omega);
     pf.phi_pref = (float)ph.phi_pref;
     pf.rho_w = (float)prm.rho_w;
+    pf.g[0] = (float)ph.g[0];
+    pf.g[1] = lattice == LBM_D2Q9 ? 0.0f : (float)ph.g[1];
+    pf.g[2] = lattice == LBM_D2Q9 ? (float)ph.g[1] : (float)ph.g[2];
     {
         // P - P0 of the solid density, in FP32
         const float r = pf.rho_w;

@@ -47,6 +47,7 @@ struct PhysF {
     float a, b, RT, aalpha;
     float kappa, omega, omw, phi_pref;  // omw = 1 - omega
     float rho_w, spsi_w;                // virtual solid density and its P - P0
+    float g[3];                         // body acceleration in the kernel frame (D2Q9: gx, 0, gy)
 };
 
 // Lattice description in the 3D frame: D2Q9 uses (cx, 0, cy).
@@ -362,7 +363,8 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                 }
                 float F[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) F[a] = -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y;
+                for (int a = 0; a < 3; ++a)   // Korteweg force plus the body force rho g
+                    F[a] = __fmaf_rn(rho, p.g[a], -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y);
                 // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2
                 const int gr0 = THREE ? ty + 1 : 0, gc0 = tx + 1;
                 float Phi[3];

@@ -25,6 +25,7 @@ struct Phys {
     double omega;             // 1 / tau
     double phi_pref;          // -(1 - omega/2), or 0 with the correction off
     double rho_w;             // virtual solid density
+    double g[3];              // body acceleration; rho g joins the force (Sec. 4.1)
 };
 
 template <int LAT> struct Lattice;
@@ -75,8 +76,8 @@ __device__ __forceinline__ double signed_psi(const Phys &p, double rho)
 __device__ __forceinline__ int wrapm(int v, int n) { return v < 0 ? v + n : v; }
 __device__ __forceinline__ int wrapp(int v, int n) { return v >= n ? v - n : v; }
 
-// Korteweg force acting on the fluid at one node:
-//   F = -2 (s psi)_c S_psi - kappa rho_c S_rho,
+// Korteweg force acting on the fluid at one node, plus the body force rho g:
+//   F = -2 (s psi)_c S_psi - kappa rho_c S_rho + rho_c g,
 //   S_psi = sum_i (w_i/cs2) c_i [4/3 psi(r+c_i) - 1/6 psi(r+2c_i)],
 //   S_rho = sum_i (w_i/cs2) c_i [2 rho(r+c_i) - rho(r+2c_i)]   (Eq. Kforce_final).
 // w_i/cs2 c_ia = 1/2 W(c_ib) W(c_ic) c_ia with the 1D weights W(0) = 2/3,
@@ -136,7 +137,7 @@ __device__ __forceinline__ void korteweg_force(const Geo &g, const Phys &p,
         }
     }
 #pragma unroll
-    for (int a = 0; a < D; ++a) F[a] = -2.0 * spsi_c * Spsi[a] - p.kappa * rho_c * Srho[a];
+    for (int a = 0; a < D; ++a) F[a] = -2.0 * spsi_c * Spsi[a] - p.kappa * rho_c * Srho[a] + rho_c * p.g[a];
 }
 
 // Moments, EOS and pseudo-potential of every fluid node; flags bad densities.

@@ -25,7 +25,8 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 
 class lbm_params(C.Structure):
     _fields_ = [("a", C.c_double), ("b", C.c_double), ("acentric", C.c_double),
-                ("rho_w", C.c_double), ("storage", C.c_int), ("flags", C.c_int)]
+                ("rho_w", C.c_double), ("storage", C.c_int), ("flags", C.c_int),
+                ("g", C.c_double * 3)]
 
 
 class LBMError(RuntimeError):
@@ -130,7 +131,7 @@ class LBM:
                  kappa: float, tau: float, mask=None, a: float | None = None,
                  b: float | None = None, acentric: float | None = None,
                  rho_w: float | None = None, flags: int = 0, storage: int = F64,
-                 stream=None, torch_memory: bool = True):
+                 stream=None, torch_memory: bool = True, g=None):
         import torch
         self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
         self.D = 2 if lattice == D2Q9 else 3
@@ -147,6 +148,9 @@ class LBM:
             p.rho_w = rho_w
         p.flags = flags
         p.storage = storage
+        if g is not None:   # body acceleration (gx, gy[, gz])
+            for a, v in enumerate(g):
+                p.g[a] = float(v)
         self.params = p
         mptr = None
         if mask is not None:

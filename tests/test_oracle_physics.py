@@ -7,6 +7,9 @@
   link beyond the last fluid node.
 - Normal-mode decay independent of the frame velocity with the correction
   Phi, frame-dependent without it or with the printed sign (Sec. 4.2).
+- Body force: single-phase Poiseuille flow between halfway bounce-back walls
+  against the parabola; the layered solution of the Sec. 4.1 equations
+  against the two-layer closed form of its appendix.
 - The initial state has the requested physical velocity U (Sec. 2.3.5), and
   a large-density-ratio drop started at rest in U stays bounded where the
   impulsive start diverges.
@@ -196,3 +199,111 @@ def test_shan_chen_flat_interface_reaches_maxwell(eos):
     o.step(3000)
     r = o.moments()[0].reshape(5, nx)[2]
     assert abs(r[0] / rv - 1) < 0.01 and abs(r[64] / rl - 1) < 0.01, (r[0] / rv, r[64] / rl)
+
+
+
+def _appendix_two_layer(y, H, hl, rl, rv, ml, mv, g, restore_bv=True):
+    """The two-layer closed form of the appendix to Sec. 4.1 (coefficients
+    b_l, b_v, c_v as printed). The printed b_v drops the term
+    -h_l^2 mu_v rho_l; restore_bv puts it back."""
+    al, av = -rl * g / (2 * ml), -rv * g / (2 * mv)
+    D = H * ml - hl * ml + hl * mv
+    bl = g * (H**2 * ml * rv - 2 * hl**2 * ml * rl + hl**2 * ml * rv + hl**2 * mv * rl
+              + 2 * H * hl * ml * rl - 2 * H * hl * ml * rv) / (2 * ml * D)
+    bv = g * (H**2 * ml * rv - hl**2 * ml * rv + 2 * hl**2 * mv * rv
+              - (hl**2 * mv * rl if restore_bv else 0.0)) / (2 * mv * D)
+    cv = g * H * (hl**2 * ml * rv + hl**2 * mv * rl - 2 * hl**2 * mv * rv - H * hl * ml * rv
+                  + H * hl * mv * rv) / (2 * mv * D)
+    return np.where(y <= hl, al * y * y + bl * y, av * y * y + bv * y + cv)
+
+
+@pytest.mark.parametrize("case", [(200.0, 100.0, 10.1, 1.0, 10.1, 1.0),     # Sec. 4.1 (a)
+                                  (200.0, 70.0, 1030.0, 1.0, 11.3, 1.0),    # Sec. 4.1 (b)
+                                  (1.0, 0.3, 2.0, 5.0, 0.7, 3.0)])
+def test_layered_solver_against_the_two_layer_appendix_solution(case):
+    """The layer solver satisfies the ODEs and interface conditions of Sec.
+    4.1 and equals the appendix's two-layer closed form once b_v's dropped
+    term is restored; with b_v as printed, u(H) = 0 fails."""
+    H, hl, rl, rv, ml, mv = case
+    g = 1e-3
+    u = ph.layered_poiseuille([(hl, rl, ml), (H - hl, rv, mv)], g)
+    y = np.linspace(0.0, H, 2001)
+    scale = np.max(np.abs(u(y)))
+    e = 1e-6 * H
+    assert abs(u(0.0)) < 1e-12 * scale and abs(u(H)) < 1e-12 * scale
+    assert abs(u(hl - e) - u(hl + e)) < 1e-5 * scale
+    du = lambda y0: (u(y0 + e / 10) - u(y0 - e / 10)) / (e / 5)
+    assert abs(ml * du(hl - e) - mv * du(hl + e)) < 1e-4 * rl * g * H   # of the stress scale
+    for y0, r, m in [(0.5 * hl, rl, ml), (0.5 * (hl + H), rv, mv)]:   # m u'' = -rho g
+        d2 = (u(y0 + e * 100) - 2 * u(y0) + u(y0 - e * 100)) / (e * 100) ** 2
+        assert m * d2 == pytest.approx(-r * g, rel=1e-3)
+    assert np.max(np.abs(_appendix_two_layer(y, H, hl, rl, rv, ml, mv, g) - u(y))) < 1e-12 * scale
+    printed = _appendix_two_layer(np.array([H]), H, hl, rl, rv, ml, mv, g, restore_bv=False)
+    assert abs(printed[0]) > 1e-3 * scale
+
+
+def test_single_phase_poiseuille_with_body_force():
+    """A uniform vapour (rho 0.5, below the vdW spinodal at T/Tc 0.8) driven
+    by g between halfway bounce-back walls: the steady U matches
+    g y'(H - y') / (2 nu) with nu = (tau - 1/2)/3 and the walls half a link
+    beyond the last fluid rows (y' = y - 1/2, H = ny - 2)."""
+    nx, ny, tau, g, rho0 = 5, 34, 1.0, 1e-6, 0.5
+    H, nu = ny - 2, (tau - 0.5) / 3.0
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = mask[-1] = 1
+    o = OracleLBM(0, nx, ny, 1, 0, 0.8, 0.0, tau, mask=mask.ravel(), a=A_VDW, rho_w=rho0,
+                  g=(g, 0.0))
+    o.init(np.full(nx * ny, rho0))
+    o.step(int(6 * H * H / nu))
+    U = o.moments()[2][: nx * ny].reshape(ny, nx)[1:-1, 2]
+    yp = np.arange(1, ny - 1) - 0.5
+    ua = g / (2 * nu) * yp * (H - yp)
+    assert np.max(np.abs(U - ua)) < 1e-3 * ua.max()
+
+
+
+def _layered_channel(H, tr=0.77):
+    """Symmetric layered channel of Sec. 4.1 configuration (a) (vdW, T/Tc
+    0.77, density and viscosity ratio 10): liquid films of H/4 on both
+    halfway-bounce-back walls (wall density rho_l, so the walls are wetted
+    by the liquid they touch), vapour in the core. Returns the set-up."""
+    a0 = 9 / 49
+    e0 = EOS(0, tr, a=a0)
+    _, rl0, _ = ph.maxwell(e0)
+    h = 1e-6 * rl0
+    a = a0 * min(1.0, 0.1 / ((e0(rl0 + h) - e0(rl0 - h)) / (2 * h)))
+    e = EOS(0, tr, a=a)
+    rv, rl, ps = ph.maxwell(e)
+    kap = ph.kappa_for_width(e, 5.0, (rv, rl, ps))
+    nx, ny = 5, H + 2
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = mask[-1] = 1
+    yp = np.arange(ny) - 0.5
+    from paper_2112_01975_gb300.inputs import tanh_interface
+    rho = np.repeat(tanh_interface(np.minimum(yp, H - yp) - H // 4, rl, rv, 5.0), nx)
+    rho[mask.ravel() == 1] = rl
+    return dict(a=a, rv=rv, rl=rl, kappa=kap, nx=nx, ny=ny, mask=mask.ravel(), rho=rho, tr=tr)
+
+
+def test_layered_channel_flow_on_the_oracle():
+    """Layered Poiseuille flow (Sec. 4.1, configuration (a)) in a channel of
+    48 rows: the steady velocity follows the momentum balance of the
+    simulated density profile within 1 % (velocity and shear stress
+    continuous through the interfaces), and the sharp-interface solution of
+    the layer equations within 15 % (interfaces of width 5 in 12-row films)."""
+    H, tau, g = 48, 1.0, 1e-6
+    nu = (tau - 0.5) / 3.0
+    c = _layered_channel(H)
+    o = OracleLBM(0, c["nx"], c["ny"], 1, 0, c["tr"], c["kappa"], tau, mask=c["mask"], a=c["a"],
+                  rho_w=c["rl"], g=(g, 0.0))
+    o.init(c["rho"])
+    o.step(int(2 * H * H / nu))
+    r, _, U, _ = o.moments()
+    rows = slice(c["nx"] + 2, (c["ny"] - 1) * c["nx"], c["nx"])      # column x = 2, fluid rows
+    Ux, rr = U[: o.N][rows], r[rows]
+    Ud = ph.channel_flow_from_profile(rr, g, nu)
+    assert np.max(np.abs(Ux - Ud)) < 0.01 * Ud.max()
+    yp = np.arange(1, H + 1) - 0.5
+    us = ph.layered_poiseuille([(H / 4, c["rl"], c["rl"] * nu), (H / 4, c["rv"], c["rv"] * nu)], g,
+                               top="symmetry")(np.minimum(yp, H - yp))
+    assert np.max(np.abs(Ux - us)) < 0.15 * us.max()
