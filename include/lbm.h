@@ -161,6 +161,17 @@ int lbm_step(lbm_handle h, int64_t n);
  * nodes report rho_w and zero velocities. Synchronises the stream. */
 int lbm_moments(lbm_handle h, double *rho, double *u, double *U, int on_device);
 
+/* Discrete pressure tensor of the current state (Appendix E): at each fluid
+ * node the populations' momentum flux sum_i c_ia c_ib f_i plus the non-local
+ * contributions of the four ring terms of the force (Eq. Kforce_final), with
+ * the force on the fluid's sign. A uniform state at rest gives P(rho) I; a
+ * resting flat interface gives a uniform normal component, and the tension
+ * sigma = integral of (P_nn - P_tt) across it (Sec. 3.2). P: double[k * N],
+ * components k = xx, yy, xy (D2Q9) or xx, yy, zz, xy, xz, yz (D3Q27), each
+ * a node plane; 0 at solid nodes. on_device: P is device memory. Synchronises;
+ * LBM_ENONFINITE if the state holds a bad density. */
+int lbm_pressure_tensor(lbm_handle h, double *P, int on_device);
+
 /* Mass sum rho and momentum sum rho u over fluid nodes (host outputs;
  * momentum has D entries), summed in a fixed order on the device.
  * Synchronises the stream. */

@@ -67,6 +67,7 @@ def lib():
         L.oracle_eos_temperature.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
         L.oracle_eos_alpha.restype = C.c_double
         L.oracle_eos_alpha.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.oracle_pressure_tensor.argtypes = [C.c_void_p, _dp]
         L.oracle_eos_pressure_array.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                                 C.c_double, _dp, C.c_long, _dp]
         _lib = L
@@ -204,6 +205,14 @@ class OracleLBM:
         out = np.empty(self.Q)
         lib().oracle_post_local(self._h, _p(b), m.ctypes.data_as(C.c_void_p), _p(out))
         return out
+
+    def pressure_tensor(self) -> np.ndarray:
+        """Discrete pressure tensor (Appendix E): [component][node] with the
+        components xx, yy[, zz], xy[, xz, yz]."""
+        na = 6 if self.D == 3 else 3
+        out = np.empty(na * self.N)
+        lib().oracle_pressure_tensor(self._h, _p(out))
+        return out.reshape(na, self.N)
 
     @property
     def RT(self) -> float:

@@ -464,6 +464,61 @@ void oracle_eos_pressure_array(int eos, double a, double b, double RT, double al
     for (long k = 0; k < n; ++k) out[k] = oracle_eos_pressure(eos, a, b, RT, alpha, rho[k]);
 }
 
+/* Discrete pressure tensor (Appendix E) of the current state, at fluid nodes:
+ *   P_ab = sum_i c_ia c_ib f_i  +  P^A + P^B + P^C + P^D,
+ * the populations' momentum flux plus the non-local contributions of the
+ * four ring terms of the force. With the force on the fluid being the
+ * negative of the printed Kforce_final (sign reading in the header), the
+ * non-local part is the negative of the printed one:
+ *   P^A =  s 4/3 psi sum_i (w_i/cs2) c_ia c_ib psi(r+c_i)
+ *   P^B = -s 1/6 [psi sum_i (w_i/cs2) c c psi(r+2c_i) + sum_i (w_i/cs2) c c psi(r-c_i) psi(r+c_i)]
+ *   P^C =  kappa rho sum_i (w_i/cs2) c c rho(r+c_i)
+ *   P^D = -kappa/2 [rho sum_i (w_i/cs2) c c rho(r+2c_i) + sum_i (w_i/cs2) c c rho(r-c_i) rho(r+c_i)]
+ * with s the sign of P - P0 at r. For a uniform state at rest it reduces to
+ * P(rho) I. Out: components xx, yy[, zz], xy[, xz, yz], each an N-plane
+ * (0 at solid nodes). Reading of the kinetic part: the paper does not state
+ * it; the populations' second moment makes P_xx uniform across a resting
+ * flat interface, rho/3 alone does not (tested). */
+void oracle_pressure_tensor(oracle_ctx *o, double *out)
+{
+    const long N = o->N;
+    const int Q = o->Q, D = o->D;
+    const int na = D == 3 ? 6 : 3;
+    const int A_[6] = {0, 1, 2, 0, 0, 1}, B_[6] = {0, 1, 2, 1, 2, 2};
+    const int A2[3] = {0, 1, 0}, B2[3] = {0, 1, 1};
+    macroscopic(o);
+    for (long z = 0; z < o->nz; ++z)
+        for (long y = 0; y < o->ny; ++y)
+            for (long x = 0; x < o->nx; ++x) {
+                long n = node_at(o, x, y, z);
+                for (int k = 0; k < na; ++k) {
+                    int al = D == 3 ? A_[k] : A2[k], be = D == 3 ? B_[k] : B2[k];
+                    if (o->mask[n]) { out[(long)k * N + n] = 0.0; continue; }
+                    double kin = 0.0, pa = 0.0, pb1 = 0.0, pb2 = 0.0, pc = 0.0, pd1 = 0.0, pd2 = 0.0;
+                    for (int i = 0; i < Q; ++i) {
+                        const int *c = o->c[i];
+                        double cc = (double)(c[al] * c[be]);
+                        kin += cc * o->f[(long)i * N + n];
+                        if (cc == 0.0) continue;
+                        double wc = o->w[i] * 3.0 * cc;
+                        long n1 = node_at(o, x + c[0], y + c[1], z + (D == 3 ? c[2] : 0));
+                        long n2 = node_at(o, x + 2 * c[0], y + 2 * c[1], z + (D == 3 ? 2 * c[2] : 0));
+                        long nm = node_at(o, x - c[0], y - c[1], z - (D == 3 ? c[2] : 0));
+                        pa += wc * o->psi[n1];
+                        pb1 += wc * o->psi[n2];
+                        pb2 += wc * o->psi[nm] * o->psi[n1];
+                        pc += wc * o->rho[n1];
+                        pd1 += wc * o->rho[n2];
+                        pd2 += wc * o->rho[nm] * o->rho[n1];
+                    }
+                    double sg = (double)o->sgn[n], ps = o->psi[n], r = o->rho[n];
+                    out[(long)k * N + n] = kin + sg * (4.0 / 3.0) * ps * pa
+                                           - sg * (1.0 / 6.0) * (ps * pb1 + pb2)
+                                           + o->kappa * r * pc - 0.5 * o->kappa * (r * pd1 + pd2);
+                }
+            }
+}
+
 /* One node's post-collision populations from its local neighbourhood, for
  * checking large lattices at sampled nodes. block[((dz*5 + dy)*5 + dx)*Q + i]
  * holds the populations of the node at offset (dx-2, dy-2, dz-2) (dz = 2 only

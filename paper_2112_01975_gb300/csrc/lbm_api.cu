@@ -407,6 +407,36 @@ int launch_macro_and_out(lbm_ctx *h, double *rho, double *u, double *U)
 }
 
 template <int LAT>
+int launch_pressure(lbm_ctx *h, double *out)
+{
+    const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
+    if (shifted(h->storage)) {
+        TempF64 t;
+        int rc = temp_alloc(h, t);
+        if (!rc) rc = decode_to<LAT>(h, h->cur, t.p);
+        if (rc) return rc;
+        lbmk::k_macro<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, t.p, h->rp, h->u,
+                                                     h->gflux, h->status);
+        lbmk::k_pressure_tensor<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, t.p, h->rp, out);
+        CU(h, cudaGetLastError());
+        CU(h, cudaStreamSynchronize(h->stream));   // before the temporary is freed
+    } else if (h->storage == LBM_F32) {
+        lbmk::k_macro<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, f32(h, h->cur),
+                                                            h->rp, h->u, h->gflux, h->status);
+        lbmk::k_pressure_tensor<LAT, float><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask,
+                                                                      f32(h, h->cur), h->rp, out);
+    } else {
+        lbmk::k_macro<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask, f64(h, h->cur), h->rp,
+                                                     h->u, h->gflux, h->status);
+        lbmk::k_pressure_tensor<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->phys, h->mask,
+                                                               f64(h, h->cur), h->rp, out);
+    }
+    CU(h, cudaGetLastError());
+    h->launches += 2;
+    return LBM_OK;
+}
+
+template <int LAT>
 int launch_init(lbm_ctx *h, const double *rho0, const double *u0)
 {
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
@@ -701,6 +731,21 @@ int lbm_moments(lbm_handle h, double *rho, double *u, double *U, int on_device)
         if (u) CU(h, cudaMemcpyAsync(u, du, sizeof(double) * D * N, cudaMemcpyDeviceToHost, h->stream));
         if (U) CU(h, cudaMemcpyAsync(U, dU, sizeof(double) * D * N, cudaMemcpyDeviceToHost, h->stream));
     }
+    return read_status(h);
+}
+
+int lbm_pressure_tensor(lbm_handle h, double *P, int on_device)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (!P) return fail(h, LBM_EINVAL, "null output");
+    const size_t N = h->geo.N, na = h->D == 3 ? 6 : 3;
+    // the dead population buffer holds (1 + 2D) N >= na N doubles
+    double *out = on_device ? P : static_cast<double *>(h->fv[h->cur ^ 1]);
+    rc = h->lattice == LBM_D2Q9 ? launch_pressure<0>(h, out) : launch_pressure<1>(h, out);
+    if (rc) return rc;
+    if (!on_device)
+        CU(h, cudaMemcpyAsync(P, out, sizeof(double) * na * N, cudaMemcpyDeviceToHost, h->stream));
     return read_status(h);
 }
 

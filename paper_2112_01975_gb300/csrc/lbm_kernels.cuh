@@ -295,6 +295,70 @@ __global__ void k_moments_out(Geo g, Phys p, const uint8_t *__restrict__ mask,
     }
 }
 
+// Discrete pressure tensor (Appendix E) at fluid nodes: the populations'
+// momentum flux sum_i c_ia c_ib f_i plus the non-local parts of the four
+// ring terms of the force, with the sign of the force on the fluid:
+//   s 4/3 psi S1[psi] - s/6 (psi S2[psi] + X[psi]) + kappa rho S1[rho]
+//   - kappa/2 (rho S2[rho] + X[rho]),
+// S_k[v] = sum_i (w_i/cs2) c_ia c_ib v(r + k c_i),
+// X[v] = sum_i (w_i/cs2) c_ia c_ib v(r - c_i) v(r + c_i).
+// Needs rp of the current state (k_macro). Components xx, yy[, zz],
+// xy[, xz, yz] as N-planes; 0 at solid nodes.
+template <int LAT, typename T = double>
+__global__ void k_pressure_tensor(Geo g, Phys p, const uint8_t *__restrict__ mask,
+                                  const T *__restrict__ f, const double2 *__restrict__ rp,
+                                  double *__restrict__ out)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q, NA = D == 3 ? 6 : 3;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned n = x + g.nx * (y + g.ny * z);
+    constexpr int CA[6] = {0, 1, D == 3 ? 2 : 0, 0, 0, 1};
+    constexpr int CB[6] = {0, 1, D == 3 ? 2 : 1, 1, 2, 2};
+    if (mask[n]) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) out[(size_t)k * g.N + n] = 0.0;
+        return;
+    }
+    double kin[NA], pa[NA], pb1[NA], pb2[NA], pc[NA], pd1[NA], pd2[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) kin[k] = pa[k] = pb1[k] = pb2[k] = pc[k] = pd1[k] = pd2[k] = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int c[3] = {cxi(i), cyi(i), D == 3 ? czi(i) : 0};
+        const double fi = (double)f[(size_t)i * g.N + n];
+        const auto at = [&](int k) {
+            const int xx = (x + k * c[0] + 2 * g.nx) % g.nx;
+            const int yy = (y + k * c[1] + 2 * g.ny) % g.ny;
+            const int zz = D == 3 ? (z + k * c[2] + 2 * g.nz) % g.nz : 0;
+            return rp[xx + g.nx * (yy + g.ny * zz)];
+        };
+        const double2 v1 = at(1), v2 = at(2), vm = at(-1);
+        const double wi = (D == 3 ? (c[0] ? 1.0 / 6.0 : 2.0 / 3.0) * (c[1] ? 1.0 / 6.0 : 2.0 / 3.0) *
+                                        (c[2] ? 1.0 / 6.0 : 2.0 / 3.0)
+                                  : (c[0] ? 1.0 / 6.0 : 2.0 / 3.0) * (c[1] ? 1.0 / 6.0 : 2.0 / 3.0)) * 3.0;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const double cc = (double)(c[CA[k]] * c[CB[k]]);
+            kin[k] += cc * fi;
+            const double wc = wi * cc;
+            pa[k] += wc * fabs(v1.y);
+            pb1[k] += wc * fabs(v2.y);
+            pb2[k] += wc * fabs(vm.y) * fabs(v1.y);
+            pc[k] += wc * v1.x;
+            pd1[k] += wc * v2.x;
+            pd2[k] += wc * vm.x * v1.x;
+        }
+    }
+    const double2 c0 = rp[n];
+    const double sg = c0.y > 0.0 ? 1.0 : -1.0, ps = fabs(c0.y), r = c0.x;
+#pragma unroll
+    for (int k = 0; k < NA; ++k)
+        out[(size_t)k * g.N + n] = kin[k] + sg * (4.0 / 3.0) * ps * pa[k] - sg * (1.0 / 6.0) * (ps * pb1[k] + pb2[k]) +
+                                   p.kappa * r * pc[k] - 0.5 * p.kappa * (r * pd1[k] + pd2[k]);
+}
+
 // Side field of the initial density: rp = (rho0, s psi(rho0)) at fluid nodes
 // (solid nodes get theirs from k_fill_solid).
 template <int LAT>

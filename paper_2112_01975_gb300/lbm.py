@@ -52,6 +52,7 @@ def _load():
     L.lbm_step.argtypes = [vp, i64]
     L.lbm_moments.argtypes = [vp, vp, vp, vp, C.c_int]
     L.lbm_reduce.argtypes = [vp, dp, dp]
+    L.lbm_pressure_tensor.argtypes = [vp, vp, C.c_int]
     L.lbm_get_populations.argtypes = [vp, vp, C.c_int]
     L.lbm_set_populations.argtypes = [vp, vp, C.c_int]
     L.lbm_sync.argtypes = [vp, C.c_int]
@@ -217,6 +218,18 @@ class LBM:
         rho, u, U = out
         self._check(_lib.lbm_moments(self._h, *(None if t is None else _ptr(t) for t in out), 1))
         return rho, u, U
+
+    def pressure_tensor(self, out=None):
+        """Discrete pressure tensor [component][node] (xx, yy[, zz], xy[, xz,
+        yz]); pass a device tensor of that many doubles to fill it on the
+        device."""
+        na = 6 if self.D == 3 else 3
+        if out is None:
+            out = np.empty(na * self.N)
+            self._check(_lib.lbm_pressure_tensor(self._h, _ptr(out), 0))
+            return out.reshape(na, self.N)
+        self._check(_lib.lbm_pressure_tensor(self._h, _ptr(out), 1))
+        return out
 
     def reduce(self):
         m = C.c_double()

@@ -63,6 +63,9 @@ def test_laplace_law_and_flat_interface_tension(lbm):
     assert np.abs(U).max() < 1e-4                              # at rest
     sigma_flat = kap * np.sum(np.gradient(rho) ** 2) + np.sum(rho * ux ** 2)
     assert slope == pytest.approx(sigma_flat, rel=0.02), (slope, sigma_flat)
+    # the same tension from the discrete pressure tensor (Appendix E), sum of P_xx - P_yy
+    P = g.pressure_tensor().reshape(3, 5, nx)[:, 2, : nx // 2]
+    assert slope == pytest.approx(float(np.sum(P[0] - P[1])), rel=0.02)
     sigma_cont = ph.surface_tension(e, kap, (rv, rl, ps))
     assert 1.0 < slope / sigma_cont < 1.25
 
@@ -154,3 +157,36 @@ def test_shan_chen_parity_coexistence_and_fp32(lbm, eos):
     g32.step(5300)
     r32 = g32.moments()[0].reshape(5, nx)[2]
     assert np.max(np.abs(r32 / r64 - 1)) < 5e-3
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_pressure_tensor_parity(lbm, lattice):
+    """lbm_pressure_tensor against the oracle's discrete pressure tensor
+    (Appendix E): FP64 storage after 150 steps to 1e-10 of the tensor's
+    scale; FP32 storage on the oracle's state (set through
+    lbm_set_populations) to 1e-4."""
+    if lattice == 1:
+        w = inputs.DROP_D3Q27_128
+        nx, ny, nz = 33, 30, 28
+        mask = inputs.block_mask(nx, ny, nz, (0, 0, 0), (nx, ny, 1))
+        rho = inputs.add_noise(inputs.drop(nx, ny, nz, 8.0, w.rho_v, w.rho_l, center=(16, 15, 12)), 1e-4, 51)
+    else:
+        w = inputs.DROP_D2Q9_64
+        nx, ny, nz = 64, 40, 1
+        mask = inputs.block_mask(nx, ny, 1, (20, 0, 0), (30, 3, 1))
+        rho = inputs.add_noise(inputs.drop(nx, ny, 1, 12.0, w.rho_v, w.rho_l), 1e-4, 52)
+    rho = np.where(mask == 1, w.rho_v, rho)
+    kw = dict(a=w.a, b=w.b, mask=mask, rho_w=w.rho_v)
+    g = lbm.LBM(lattice, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, 0.9, **kw)
+    o = OracleLBM(lattice, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, 0.9, **kw)
+    g.init(rho)
+    o.init(rho)
+    g.step(150)
+    o.step(150)
+    Po = o.pressure_tensor()
+    scale = float(np.max(np.abs(Po)))
+    assert np.max(np.abs(g.pressure_tensor() - Po)) < 1e-10 * scale
+    g32 = lbm.LBM(lattice, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, 0.9, storage=lbm.F32, **kw)
+    g32.init(rho)
+    g32.set_populations(o.get_populations())
+    assert np.max(np.abs(g32.pressure_tensor() - Po)) < 1e-4 * scale

@@ -307,3 +307,45 @@ def test_layered_channel_flow_on_the_oracle():
     us = ph.layered_poiseuille([(H / 4, c["rl"], c["rl"] * nu), (H / 4, c["rv"], c["rv"] * nu)], g,
                                top="symmetry")(np.minimum(yp, H - yp))
     assert np.max(np.abs(Ux - us)) < 0.15 * us.max()
+
+
+@pytest.mark.parametrize("lattice,eos,rho0", [(0, 0, 0.5), (1, 1, 8.3)])
+def test_pressure_tensor_of_a_uniform_state(lattice, eos, rho0):
+    """Discrete pressure tensor (Appendix E) of a uniform state moving at U:
+    the EOS pressure plus the momentum flux, P = P(rho) I + rho U U, to
+    rounding (a vdW vapour and a PR liquid, both outside the spinodal)."""
+    nz = 6 if lattice == 1 else 1
+    o = OracleLBM(lattice, 7, 6, nz, eos, 0.7, 0.02, 1.0)
+    N, D = o.N, o.D
+    Uv = [0.03, -0.02, 0.01][:D]
+    o.init(np.full(N, rho0), np.concatenate([np.full(N, v) for v in Uv]))
+    P = o.pressure_tensor()
+    p = EOS(eos, 0.7)(rho0)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)] if D == 3 else [(0, 0), (1, 1), (0, 1)]
+    for k, (a, b) in enumerate(pairs):
+        want = (p if a == b else 0.0) + rho0 * Uv[a] * Uv[b]
+        assert np.max(np.abs(P[k] - want)) < 1e-13 * max(abs(p), 1.0), (a, b)
+
+
+def test_flat_interface_pressure_tensor():
+    """At a resting flat interface the normal component P_xx of the discrete
+    pressure tensor is uniform through the interface (the paper's point in
+    Appendix E), P_xy vanishes, and sigma = sum (P_xx - P_yy) per interface
+    equals kappa int rho_x^2 + int rho u_x^2, the tension the Laplace law
+    measures here (the second term is the momentum flux of the bare velocity
+    u = -F/(2 rho) of the resting interface)."""
+    e = EOS(0, 0.8, a=A_VDW)
+    rv, rl, ps = ph.maxwell(e)
+    kap = ph.kappa_for_width(e, 5.0, (rv, rl, ps))
+    nx, ny = 128, 5
+    o = OracleLBM(0, nx, ny, 1, 0, 0.8, kap, 1.0, a=A_VDW)
+    o.init(slab(nx, ny, 1, 32, 96, rv, rl, 5.0))
+    o.step(6000)
+    P = o.pressure_tensor().reshape(3, ny, nx)[:, 2]
+    r, u, _, _ = o.moments()
+    rho, ux = r.reshape(ny, nx)[2], u[: nx * ny].reshape(ny, nx)[2]
+    assert np.ptp(P[0]) < 1e-3 * ps
+    assert np.max(np.abs(P[2])) < 1e-12 * ps
+    sigma = np.sum(P[0] - P[1]) / 2
+    sigma_int = (kap * np.sum(np.gradient(rho) ** 2) + np.sum(rho * ux ** 2)) / 2
+    assert sigma == pytest.approx(sigma_int, rel=0.01)
