@@ -129,15 +129,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def oracle_sample_mlups(w, target_s: float = 12.0):
-    """Single-thread FP64 oracle throughput on a centred crop of the workload."""
+def oracle_sample_mlups(w, target_s: float = 12.0, openmp: bool = False):
+    """FP64 oracle throughput on a centred crop of the workload: one host
+    thread, or (openmp) the -fopenmp build of the same source on all cores."""
     from oracle.lbm import OracleLBM
     from paper_2112_01975_gb300 import inputs
     n = 48 if w.lattice == 1 else 64
     nz = n if w.lattice == 1 else 1
     rho = inputs.add_noise(inputs.drop(n, n, nz, w.radius * n / w.nx, w.rho_v, w.rho_l),
                            w.noise, w.seed)
-    o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b)
+    o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
+                  openmp=openmp)
     o.init(rho)
     o.step(1)
     steps, t0 = 0, time.perf_counter()
@@ -370,6 +372,13 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         v, sample = oracle_sample_mlups(w)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+        try:   # the same oracle built with -fopenmp, all host cores
+            va, sa = oracle_sample_mlups(w, target_s=6.0, openmp=True)
+            cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            cpu["all_cores"] = {"value": va, "unit": "MLUPS", "cores": cores,
+                                "kind": "oracle, -fopenmp build", "sample": sa}
+        except Exception as exc:   # no OpenMP in the host compiler
+            cpu["all_cores"] = {"unavailable": str(exc)[:200]}
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,

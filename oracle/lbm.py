@@ -29,14 +29,15 @@ DEFAULT_AB = {EOS_VDW: (9.0 / 49.0, 2.0 / 21.0), EOS_PR: (2.0 / 49.0, 2.0 / 21.0
               EOS_SC1: (1.0, 0.1), EOS_SC2: (1.0, 0.1)}
 DEFAULT_ACENTRIC = 0.344
 
-_lib = None
+_libs = {}
 _dp = C.POINTER(C.c_double)
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(_build.build())
+def lib(openmp: bool = False):
+    """The oracle library; openmp=True loads the -fopenmp build of the same
+    source (all host cores, same results bit for bit)."""
+    if openmp not in _libs:
+        L = C.CDLL(_build.build(openmp=openmp))
         L.oracle_create.restype = C.c_void_p
         L.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                     C.c_double, C.c_double, C.c_void_p, C.c_double,
@@ -70,8 +71,8 @@ def lib():
         L.oracle_pressure_tensor.argtypes = [C.c_void_p, _dp]
         L.oracle_eos_pressure_array.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                                 C.c_double, _dp, C.c_long, _dp]
-        _lib = L
-    return _lib
+        _libs[openmp] = L
+    return _libs[openmp]
 
 
 def _p(a: np.ndarray):
@@ -110,9 +111,11 @@ class OracleLBM:
                  kappa: float, tau: float, mask: np.ndarray | None = None,
                  a: float | None = None, b: float | None = None,
                  acentric: float = DEFAULT_ACENTRIC, rho_w: float = 1.0, flags: int = 0,
-                 g=(0.0, 0.0, 0.0)):
+                 g=(0.0, 0.0, 0.0), openmp: bool = False):
         """g: body acceleration (gx, gy[, gz]); the force rho g is added to the
-        Korteweg force (the generic F of Eq. LBGK)."""
+        Korteweg force (the generic F of Eq. LBGK). openmp: run on the
+        -fopenmp build (all host cores, same results)."""
+        self._L = lib(openmp)
         self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
         self.D = 2 if lattice == 0 else 3
         self.Q = 9 if lattice == 0 else 27
@@ -127,7 +130,7 @@ class OracleLBM:
             assert self._mask.size == self.N
             mp = self._mask.ctypes.data_as(C.c_void_p)
         gg = tuple(g) + (0.0,) * (3 - len(g))
-        self._h = lib().oracle_create(lattice, nx, ny, nz, eos, t_over_tc, kappa, tau, mp,
+        self._h = self._L.oracle_create(lattice, nx, ny, nz, eos, t_over_tc, kappa, tau, mp,
                                       a, b, acentric, rho_w, flags, *map(float, gg))
         if not self._h:
             raise ValueError("oracle_create rejected the arguments")
@@ -135,66 +138,66 @@ class OracleLBM:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().oracle_destroy(h)
+            self._L.oracle_destroy(h)
             self._h = None
 
     def init(self, rho0: np.ndarray, u0: np.ndarray | None = None):
         r = np.ascontiguousarray(rho0, dtype=np.float64)
         u = np.ascontiguousarray(u0 if u0 is not None else np.zeros(self.D * self.N),
                                  dtype=np.float64)
-        lib().oracle_init(self._h, _p(r), _p(u))
+        self._L.oracle_init(self._h, _p(r), _p(u))
 
     def step(self, n: int = 1):
-        lib().oracle_step(self._h, n)
+        self._L.oracle_step(self._h, n)
 
     def moments(self):
         rho = np.empty(self.N)
         u = np.empty(self.D * self.N)
         U = np.empty(self.D * self.N)
         F = np.empty(self.D * self.N)
-        lib().oracle_moments(self._h, _p(rho), _p(u), _p(U), _p(F))
+        self._L.oracle_moments(self._h, _p(rho), _p(u), _p(U), _p(F))
         return rho, u, U, F
 
     def reduce(self):
         m = C.c_double()
         j = np.zeros(3)
-        lib().oracle_reduce(self._h, C.byref(m), _p(j))
+        self._L.oracle_reduce(self._h, C.byref(m), _p(j))
         return m.value, j[: self.D].copy()
 
     def get_populations(self) -> np.ndarray:
         out = np.empty(self.Q * self.N)
-        lib().oracle_get_populations(self._h, _p(out))
+        self._L.oracle_get_populations(self._h, _p(out))
         return out
 
     def set_populations(self, f: np.ndarray):
         f = np.ascontiguousarray(f, dtype=np.float64)
         assert f.size == self.Q * self.N
-        lib().oracle_set_populations(self._h, _p(f))
+        self._L.oracle_set_populations(self._h, _p(f))
 
     def feq(self, rho: float, u) -> np.ndarray:
         uu = np.zeros(3)
         uu[: self.D] = u
         out = np.empty(self.Q)
-        lib().oracle_feq(self._h, rho, _p(uu), _p(out))
+        self._L.oracle_feq(self._h, rho, _p(uu), _p(out))
         return out
 
     def fstar(self, rho: float, u, F, Phi) -> np.ndarray:
         uu, FF, PP = np.zeros(3), np.zeros(3), np.zeros(3)
         uu[: self.D], FF[: self.D], PP[: self.D] = u, F, Phi
         out = np.empty(self.Q)
-        lib().oracle_fstar(self._h, rho, _p(uu), _p(FF), _p(PP), _p(out))
+        self._L.oracle_fstar(self._h, rho, _p(uu), _p(FF), _p(PP), _p(out))
         return out
 
     def stencil(self, g: np.ndarray, g1: float, g2: float) -> np.ndarray:
         g = np.ascontiguousarray(g, dtype=np.float64)
         out = np.zeros(3 * self.N)
-        lib().oracle_stencil(self._h, _p(g), g1, g2, _p(out))
+        self._L.oracle_stencil(self._h, _p(g), g1, g2, _p(out))
         return out[: self.D * self.N].copy()
 
     def weights(self):
         w = np.empty(self.Q)
         c = np.empty(3 * self.Q, dtype=np.int32)
-        lib().oracle_weights(self._h, _p(w), c.ctypes.data_as(C.POINTER(C.c_int)))
+        self._L.oracle_weights(self._h, _p(w), c.ctypes.data_as(C.POINTER(C.c_int)))
         return w, c.reshape(self.Q, 3)
 
     def post_local(self, block: np.ndarray, mblock: np.ndarray) -> np.ndarray:
@@ -203,7 +206,7 @@ class OracleLBM:
         b = np.ascontiguousarray(block, dtype=np.float64)
         m = np.ascontiguousarray(mblock, dtype=np.uint8)
         out = np.empty(self.Q)
-        lib().oracle_post_local(self._h, _p(b), m.ctypes.data_as(C.c_void_p), _p(out))
+        self._L.oracle_post_local(self._h, _p(b), m.ctypes.data_as(C.c_void_p), _p(out))
         return out
 
     def pressure_tensor(self) -> np.ndarray:
@@ -211,9 +214,9 @@ class OracleLBM:
         components xx, yy[, zz], xy[, xz, yz]."""
         na = 6 if self.D == 3 else 3
         out = np.empty(na * self.N)
-        lib().oracle_pressure_tensor(self._h, _p(out))
+        self._L.oracle_pressure_tensor(self._h, _p(out))
         return out.reshape(na, self.N)
 
     @property
     def RT(self) -> float:
-        return lib().oracle_rt(self._h)
+        return self._L.oracle_rt(self._h)

@@ -50,6 +50,11 @@
  *    velocity u = U0 - F(rho0)/(2 rho0), so that the flow starts with the
  *    requested physical velocity U0 (oracle_init).
  *
+ * The node loops carry OpenMP pragmas: every iteration writes its own
+ * entries, so a build with -fopenmp (the all-cores CPU baseline) gives the
+ * same results bit for bit; the plain build ignores them. Reductions stay
+ * serial.
+ *
  * Lattice units: dr = dt = 1, cs2 = 1/3, R = 1.
  * Direction index i = (cx+1) + 3(cy+1) [+ 9(cz+1)], opposite = Q-1-i.
  * Populations f[i*N + n], node n = x + nx*(y + ny*z).
@@ -251,6 +256,7 @@ void oracle_fstar(const oracle_ctx *o, double rho, const double *u, const double
  * periodic wrap. out holds D planes of N. */
 void oracle_stencil(const oracle_ctx *o, const double *g, double g1, double g2, double *out)
 {
+    #pragma omp parallel for collapse(2)
     for (long z = 0; z < o->nz; ++z)
         for (long y = 0; y < o->ny; ++y)
             for (long x = 0; x < o->nx; ++x) {
@@ -273,6 +279,7 @@ static void force_from_density(oracle_ctx *o)
     long N = o->N;
     int D = o->D;
     /* equation of state and pseudo-potential, Sec. 2.3.4 with P0 = rho/3 */
+    #pragma omp parallel for
     for (long n = 0; n < N; ++n) {
         double rho = o->rho[n];
         double P = oracle_eos_pressure(o->eos, o->a, o->b, o->RT, o->alpha, rho);
@@ -286,6 +293,7 @@ static void force_from_density(oracle_ctx *o)
     oracle_stencil(o, o->psi, 4.0 / 3.0, -1.0 / 6.0, Spsi);
     oracle_stencil(o, o->rho, 2.0, -1.0, Srho);
     double fs = (o->flags & ORACLE_FORCE_PRINTED_SIGN) ? 1.0 : -1.0;
+    #pragma omp parallel for
     for (long n = 0; n < N; ++n)
         for (int al = 0; al < 3; ++al) {
             long k = al * N + n;
@@ -303,6 +311,7 @@ static void macroscopic(oracle_ctx *o)
     long N = o->N;
     int Q = o->Q, D = o->D;
     /* moments, Sec. 2.3.3 */
+    #pragma omp parallel for
     for (long n = 0; n < N; ++n) {
         if (o->mask[n]) {
             o->rho[n] = o->rho_w;
@@ -322,6 +331,7 @@ static void macroscopic(oracle_ctx *o)
     /* correction term, Eq. correction with P0 = rho/3 (sign reading in the header) */
     double pref = (o->flags & ORACLE_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * o->omega);
     if (o->flags & ORACLE_PHI_PRINTED_SIGN) pref = -pref;
+    #pragma omp parallel for collapse(2)
     for (long z = 0; z < o->nz; ++z)
         for (long y = 0; y < o->ny; ++y)
             for (long x = 0; x < o->nx; ++x) {
@@ -350,6 +360,7 @@ static void step_once(oracle_ctx *o)
     int Q = o->Q, D = o->D;
     macroscopic(o);
     double feq[27], fst[27];
+    #pragma omp parallel for collapse(2) private(feq, fst)
     for (long z = 0; z < o->nz; ++z)
         for (long y = 0; y < o->ny; ++y)
             for (long x = 0; x < o->nx; ++x) {
@@ -487,6 +498,7 @@ void oracle_pressure_tensor(oracle_ctx *o, double *out)
     const int A_[6] = {0, 1, 2, 0, 0, 1}, B_[6] = {0, 1, 2, 1, 2, 2};
     const int A2[3] = {0, 1, 0}, B2[3] = {0, 1, 1};
     macroscopic(o);
+    #pragma omp parallel for collapse(2)
     for (long z = 0; z < o->nz; ++z)
         for (long y = 0; y < o->ny; ++y)
             for (long x = 0; x < o->nx; ++x) {

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle.lbm import OracleLBM, ZETA_LITERAL
+from paper_2112_01975_gb300 import inputs
 
 RNG = np.random.default_rng(12345)
 
@@ -274,3 +275,31 @@ def test_node_local_post_matches_full_step(lattice):
         post = o.post_local(block, mask[idx])
         for i, (j, d) in enumerate(sample.pushed_indices(shape, x, y, z, c, mask)):
             assert post[i] == pytest.approx(f1[j, d], rel=1e-14, abs=1e-16)
+
+
+def test_openmp_build_is_bitwise_the_plain_oracle():
+    """The -fopenmp build of the oracle (the all-cores CPU baseline) runs the
+    same node loops on several threads; every iteration writes its own
+    entries, so populations, moments and the pressure tensor are bitwise
+    those of the plain build (masked D3Q27 drop with a body force)."""
+    from oracle import build as obuild
+    try:
+        obuild.build(openmp=True)
+    except Exception as exc:   # no OpenMP in this compiler
+        pytest.skip(f"no -fopenmp build: {exc}")
+    w = inputs.DROP_D3Q27_128
+    nx, ny, nz = 20, 18, 16
+    mask = inputs.block_mask(nx, ny, nz, (0, 0, 0), (nx, ny, 1))
+    rho = inputs.add_noise(inputs.drop(nx, ny, nz, 5.0, w.rho_v, w.rho_l, center=(10, 9, 8)), 1e-4, 61)
+    rho = np.where(mask == 1, w.rho_v, rho)
+    out = []
+    for omp in (False, True):
+        o = OracleLBM(1, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, 0.8, mask=mask, a=w.a, b=w.b,
+                      rho_w=w.rho_v, g=(1e-6, 0.0, -1e-5), openmp=omp)
+        o.init(rho)
+        o.step(30)
+        out.append((o.get_populations(), o.moments(), o.pressure_tensor()))
+    assert np.array_equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][2], out[1][2])
