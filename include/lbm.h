@@ -104,12 +104,23 @@ typedef struct {
                       rho g joins the Korteweg force in xi* and in U (the generic
                       force F of Eq. LBGK; Sec. 4.1 drives layered Poiseuille
                       flow with it). Must be finite; default 0. */
+    double tau_v;        /* > 0: density-dependent relaxation. The kinematic
+                            viscosity nu = (tau - 1/2)/3 goes linearly in rho
+                            from the liquid value (the tau of lbm_create) at
+                            visc_rho[1] to the vapour value (tau_v) at
+                            visc_rho[0], constant beyond; omega, and the
+                            (1 - omega/2) of Eq. correction, per node. The
+                            paper sets a vapour to liquid viscosity ratio
+                            (Sec. 6) without the interpolation. 0 (default):
+                            one tau everywhere. Else must exceed 1/2, and
+                            0 < visc_rho[0] < visc_rho[1]. */
+    double visc_rho[2];  /* rho_v, rho_l of the interpolation */
 } lbm_params;
 
 /* Fill p with the defaults of an EOS: vdW a = 9/49, b = 2/21; PR and RKS
  * a = 2/49, b = 2/21; CS a = 1, b = 4; Shan-Chen a = b = 1 (unused);
- * acentric 0.344; rho_w = 1; LBM_F64; no flags; g = 0. Returns LBM_EINVAL
- * for an unknown eos. */
+ * acentric 0.344; rho_w = 1; LBM_F64; no flags; g = 0; tau_v = 0 (one
+ * relaxation time). Returns LBM_EINVAL for an unknown eos. */
 int lbm_default_params(int eos, lbm_params *p);
 
 /* Create a handle for one lattice. lattice: enum lbm_lattice. nx, ny, nz:

@@ -69,6 +69,7 @@ def lib(openmp: bool = False):
         L.oracle_eos_alpha.restype = C.c_double
         L.oracle_eos_alpha.argtypes = [C.c_int, C.c_double, C.c_double]
         L.oracle_pressure_tensor.argtypes = [C.c_void_p, _dp]
+        L.oracle_set_viscosity.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
         L.oracle_eos_pressure_array.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                                 C.c_double, _dp, C.c_long, _dp]
         _libs[openmp] = L
@@ -111,10 +112,12 @@ class OracleLBM:
                  kappa: float, tau: float, mask: np.ndarray | None = None,
                  a: float | None = None, b: float | None = None,
                  acentric: float = DEFAULT_ACENTRIC, rho_w: float = 1.0, flags: int = 0,
-                 g=(0.0, 0.0, 0.0), openmp: bool = False):
+                 g=(0.0, 0.0, 0.0), openmp: bool = False, tau_v: float = 0.0,
+                 visc_rho=(0.0, 1.0)):
         """g: body acceleration (gx, gy[, gz]); the force rho g is added to the
         Korteweg force (the generic F of Eq. LBGK). openmp: run on the
-        -fopenmp build (all host cores, same results)."""
+        -fopenmp build (all host cores, same results). tau_v > 0: vapour
+        relaxation time, nu linear in rho between visc_rho = (rho_v, rho_l)."""
         self._L = lib(openmp)
         self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
         self.D = 2 if lattice == 0 else 3
@@ -134,6 +137,9 @@ class OracleLBM:
                                       a, b, acentric, rho_w, flags, *map(float, gg))
         if not self._h:
             raise ValueError("oracle_create rejected the arguments")
+        if tau_v > 0.0:
+            self._L.oracle_set_viscosity(self._h, float(tau_v), float(visc_rho[0]),
+                                         float(visc_rho[1]))
 
     def __del__(self):
         h = getattr(self, "_h", None)

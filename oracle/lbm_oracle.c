@@ -79,6 +79,7 @@ typedef struct {
     double a, b, acentric, RTc, RT, alpha;
     double kappa, omega, rho_w;
     double g[3];      /* body acceleration: force rho g added to F (Sec. 4.1) */
+    double tau_v, visc_rv, visc_rl;   /* density-dependent relaxation (tau_v > 0) */
     int flags;
     unsigned char *mask;
     double *f, *fnew;
@@ -161,6 +162,21 @@ static long wrap(long v, long n) { return ((v % n) + n) % n; }
 static long node_at(const oracle_ctx *o, long x, long y, long z)
 {
     return wrap(x, o->nx) + o->nx * (wrap(y, o->ny) + o->ny * wrap(z, o->nz));
+}
+
+/* Relaxation rate at density rho. One tau for all nodes unless tau_v > 0:
+ * then the kinematic viscosity nu = (tau - 1/2)/3 goes linearly in rho from
+ * its liquid value at rho_l (the tau of oracle_create) to its vapour value
+ * at rho_v (tau_v), held constant beyond them (the paper sets a vapour to
+ * liquid viscosity ratio, Sec. 6, without stating the interpolation). */
+static double omega_at(const oracle_ctx *o, double rho)
+{
+    if (!(o->tau_v > 0.0)) return o->omega;
+    double nl = (1.0 / o->omega - 0.5) / 3.0, nv = (o->tau_v - 0.5) / 3.0;
+    double t = (o->visc_rl - rho) / (o->visc_rl - o->visc_rv);
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return 1.0 / (3.0 * (nl + (nv - nl) * t) + 0.5);
 }
 
 oracle_ctx *oracle_create(int lattice, int nx, int ny, int nz, int eos, double t_over_tc,
@@ -328,9 +344,9 @@ static void macroscopic(oracle_ctx *o)
         for (int al = 0; al < 3; ++al) o->u[al * N + n] = al < D ? j[al] / rho : 0.0;
     }
     force_from_density(o);
-    /* correction term, Eq. correction with P0 = rho/3 (sign reading in the header) */
-    double pref = (o->flags & ORACLE_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * o->omega);
-    if (o->flags & ORACLE_PHI_PRINTED_SIGN) pref = -pref;
+    /* correction term, Eq. correction with P0 = rho/3 (sign reading in the header);
+     * the omega of (1 - omega/2) is the node's own */
+    double psg = (o->flags & ORACLE_PHI_OFF) ? 0.0 : ((o->flags & ORACLE_PHI_PRINTED_SIGN) ? 1.0 : -1.0);
     #pragma omp parallel for collapse(2)
     for (long z = 0; z < o->nz; ++z)
         for (long y = 0; y < o->ny; ++y)
@@ -346,6 +362,7 @@ static void macroscopic(oracle_ctx *o)
                     double up = o->u[al * N + np], um = o->u[al * N + nm];
                     double gp = o->rho[np] * up * up * up;
                     double gm = o->rho[nm] * um * um * um;
+                    double pref = psg * (1.0 - 0.5 * omega_at(o, o->rho[n]));
                     o->Phi[k] = pref * 0.5 * (gp - gm);
                 }
             }
@@ -374,9 +391,10 @@ static void step_once(oracle_ctx *o)
                 }
                 oracle_feq(o, o->rho[n], u, feq);
                 oracle_fstar(o, o->rho[n], u, F, Phi, fst);
+                const double om = omega_at(o, o->rho[n]);
                 for (int i = 0; i < Q; ++i) {
                     double fi = o->f[(long)i * N + n];
-                    double post = fi + o->omega * (feq[i] - fi) + (fst[i] - feq[i]);
+                    double post = fi + om * (feq[i] - fi) + (fst[i] - feq[i]);
                     const int *c = o->c[i];
                     long dst = node_at(o, x + c[0], y + c[1], z + (D == 3 ? c[2] : 0));
                     if (o->mask[dst]) o->fnew[(long)(Q - 1 - i) * N + n] = post;
@@ -410,6 +428,15 @@ void oracle_init(oracle_ctx *o, const double *rho0, const double *u0)
         oracle_feq(o, rho0[n], u, feq);
         for (int i = 0; i < o->Q; ++i) o->f[(long)i * N + n] = feq[i];
     }
+}
+
+/* Density-dependent relaxation: vapour relaxation time tau_v (> 0; 0 turns
+ * it off) and the densities rho_v < rho_l between which nu is interpolated. */
+void oracle_set_viscosity(oracle_ctx *o, double tau_v, double rho_v, double rho_l)
+{
+    o->tau_v = tau_v;
+    o->visc_rv = rho_v;
+    o->visc_rl = rho_l;
 }
 
 void oracle_step(oracle_ctx *o, long nsteps)
@@ -583,7 +610,8 @@ void oracle_post_local(const oracle_ctx *o, const double *block, const unsigned 
     }
     double fs = (o->flags & ORACLE_FORCE_PRINTED_SIGN) ? 1.0 : -1.0;
     double F[3] = {0.0, 0.0, 0.0}, Phi[3] = {0.0, 0.0, 0.0}, uc[3] = {0.0, 0.0, 0.0};
-    double pref = (o->flags & ORACLE_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * o->omega);
+    const double om = omega_at(o, rho[c0]);
+    double pref = (o->flags & ORACLE_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * om);
     if (o->flags & ORACLE_PHI_PRINTED_SIGN) pref = -pref;
     for (int al = 0; al < D; ++al) {
         F[al] = fs * (sgn[c0] * 2.0 * psi[c0] * Spsi[al] + o->kappa * rho[c0] * Srho[al])
@@ -601,7 +629,7 @@ void oracle_post_local(const oracle_ctx *o, const double *block, const unsigned 
     oracle_fstar(o, rho[c0], uc, F, Phi, fst);
     for (int i = 0; i < Q; ++i) {
         double fi = block[(long)c0 * Q + i];
-        out[i] = fi + o->omega * (feq[i] - fi) + (fst[i] - feq[i]);
+        out[i] = fi + om * (feq[i] - fi) + (fst[i] - feq[i]);
     }
 #undef LIDX
 }

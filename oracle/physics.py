@@ -165,19 +165,21 @@ def layered_poiseuille(layers, g: float, top: str = "wall"):
     return u
 
 
-def channel_flow_from_profile(rho_rows, g: float, nu: float):
+def channel_flow_from_profile(rho_rows, g: float, nu):
     """Steady U(y) of body-force-driven flow along a channel mirrored about
     its mid-plane, for a density profile across it (rho at the fluid rows,
     halfway walls half a row beyond the first and last): the momentum
     balance d/dy(rho nu dU/dy) + rho g = 0 of a parallel flow, integrated
     row by row. A flat interface adds no shear stress (the Korteweg tensor
     has no xy part when rho varies along y only), so this is the diffuse-
-    interface counterpart of layered_poiseuille. Even row count assumed."""
+    interface counterpart of layered_poiseuille. nu: a number, or the
+    kinematic viscosity of each row. Even row count assumed."""
     r = np.asarray(rho_rows, dtype=float)
+    mu = r * np.broadcast_to(np.asarray(nu, dtype=float), r.shape)
     m = len(r) // 2
     U = np.zeros(len(r))
-    U[0] = 0.5 * g * np.sum(r[:m]) / (nu * r[0])          # wall to the first row
+    U[0] = 0.5 * g * np.sum(r[:m]) / mu[0]                # wall to the first row
     for j in range(1, m):
-        U[j] = U[j - 1] + g * np.sum(r[j:m]) / (nu * 0.5 * (r[j - 1] + r[j]))
+        U[j] = U[j - 1] + g * np.sum(r[j:m]) / (0.5 * (mu[j - 1] + mu[j]))
     U[m:] = U[:m][::-1]
     return U

@@ -524,6 +524,9 @@ int lbm_default_params(int eos, lbm_params *p)
     p->acentric = 0.344;
     p->rho_w = 1.0;
     p->g[0] = p->g[1] = p->g[2] = 0.0;
+    p->tau_v = 0.0;
+    p->visc_rho[0] = 0.0;
+    p->visc_rho[1] = 1.0;
     p->storage = LBM_F64;
     p->flags = 0;
     return LBM_OK;
@@ -554,6 +557,9 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     if (!(prm.a > 0.0) || !(prm.b > 0.0) || !(prm.rho_w > 0.0)) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(prm.g[a])) return LBM_EINVAL;
+    if (prm.tau_v != 0.0 && !(prm.tau_v > 0.5 && prm.visc_rho[0] > 0.0 &&
+                              prm.visc_rho[1] > prm.visc_rho[0] && std::isfinite(prm.tau_v)))
+        return LBM_EINVAL;
     lbm_ctx *h = new (std::nothrow) lbm_ctx();
     if (!h) return LBM_ENOMEM;
     h->lattice = lattice;
@@ -576,6 +582,12 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     ph.phi_pref = (prm.flags & LBM_FLAG_PHI_OFF) ? 0.0 : -(1.0 - 0.5 * ph.omega);
     ph.rho_w = prm.rho_w;
     for (int a = 0; a < 3; ++a) ph.g[a] = (a < (lattice == LBM_D2Q9 ? 2 : 3)) ? prm.g[a] : 0.0;
+    ph.var_visc = prm.tau_v > 0.0 ? 1 : 0;
+    ph.nu_l = (tau - 0.5) / 3.0;
+    ph.nu_v = ph.var_visc ? (prm.tau_v - 0.5) / 3.0 : ph.nu_l;
+    ph.visc_rv = prm.visc_rho[0];
+    ph.visc_rl = prm.visc_rho[1];
+    ph.phi_sign = (prm.flags & LBM_FLAG_PHI_OFF) ? 0.0 : -1.0;
     // FP32 fused step: D2Q9 runs in the 3D frame with one y row.
     h->geof.nx = nx;
     h->geof.ny = lattice == LBM_D2Q9 ? 1 : ny;
@@ -596,6 +608,12 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     pf.g[0] = (float)ph.g[0];
     pf.g[1] = lattice == LBM_D2Q9 ? 0.0f : (float)ph.g[1];
     pf.g[2] = lattice == LBM_D2Q9 ? (float)ph.g[1] : (float)ph.g[2];
+    pf.var_visc = ph.var_visc;
+    pf.nu_l = (float)ph.nu_l;
+    pf.nu_v = (float)ph.nu_v;
+    pf.visc_rl = (float)ph.visc_rl;
+    pf.inv_drho = ph.var_visc ? (float)(1.0 / (ph.visc_rl - ph.visc_rv)) : 0.0f;
+    pf.phi_sign = (float)ph.phi_sign;
     {
         // P - P0 of the solid density, in FP32
         const float r = pf.rho_w;

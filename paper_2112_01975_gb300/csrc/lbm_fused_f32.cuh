@@ -48,7 +48,17 @@ struct PhysF {
     float kappa, omega, omw, phi_pref;  // omw = 1 - omega
     float rho_w, spsi_w;                // virtual solid density and its P - P0
     float g[3];                         // body acceleration in the kernel frame (D2Q9: gx, 0, gy)
+    int var_visc;                       // density-dependent relaxation (nu linear in rho)
+    float nu_l, nu_v, visc_rl, inv_drho, phi_sign;   // inv_drho = 1 / (rho_l - rho_v)
 };
+
+// Relaxation rate at density rho: nu from nu_l at rho_l to nu_v at rho_v,
+// linear in rho and constant beyond (used only when var_visc).
+__device__ __forceinline__ float omega_var_f(const PhysF &p, float rho)
+{
+    const float t = fminf(fmaxf((p.visc_rl - rho) * p.inv_drho, 0.0f), 1.0f);
+    return __frcp_rn(3.0f * fmaf(p.nu_v - p.nu_l, t, p.nu_l) + 0.5f);
+}
 
 // Lattice description in the 3D frame: D2Q9 uses (cx, 0, cy).
 template <int LAT> struct LatF;
@@ -365,14 +375,17 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
 #pragma unroll
                 for (int a = 0; a < 3; ++a)   // Korteweg force plus the body force rho g
                     F[a] = __fmaf_rn(rho, p.g[a], -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y);
-                // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2
+                // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2, the node's omega
+                const float om = p.var_visc ? omega_var_f(p, rho) : p.omega;
+                const float pref = p.var_visc ? p.phi_sign * (1.0f - 0.5f * om) : p.phi_pref;
+                const float omw = p.var_visc ? 1.0f - om : p.omw;
                 const int gr0 = THREE ? ty + 1 : 0, gc0 = tx + 1;
                 float Phi[3];
-                Phi[0] = p.phi_pref * 0.5f * (s_g[pc % GS][0][gr0][gc0 + 1] - s_g[pc % GS][0][gr0][gc0 - 1]);
-                Phi[1] = THREE ? p.phi_pref * 0.5f *
+                Phi[0] = pref * 0.5f * (s_g[pc % GS][0][gr0][gc0 + 1] - s_g[pc % GS][0][gr0][gc0 - 1]);
+                Phi[1] = THREE ? pref * 0.5f *
                                      (s_g[pc % GS][1][gr0 + 1][gc0] - s_g[pc % GS][1][gr0 - 1][gc0])
                                : 0.0f;
-                Phi[2] = p.phi_pref * 0.5f *
+                Phi[2] = pref * 0.5f *
                          (s_g[(pc + 1) % GS][2][gr0][gc0] - s_g[(pc - 1) % GS][2][gr0][gc0]);
                 // momentum of the node by x-row sums
                 constexpr int R = Q / 3;
@@ -423,8 +436,8 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
                     const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
-                    const float post = SHIFT ? fmaf(p.omw, fi[i] - es.x, es.y) - weight_f<LAT>(i) * rho
-                                             : fmaf(p.omw, fi[i] - es.x, es.y);
+                    const float post = SHIFT ? fmaf(omw, fi[i] - es.x, es.y) - weight_f<LAT>(i) * rho
+                                             : fmaf(omw, fi[i] - es.x, es.y);
                     const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
                                          plane * (unsigned)Z[cz + 1];
                     if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = from_f<ST>(post);

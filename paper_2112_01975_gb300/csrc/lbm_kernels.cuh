@@ -26,7 +26,20 @@ struct Phys {
     double phi_pref;          // -(1 - omega/2), or 0 with the correction off
     double rho_w;             // virtual solid density
     double g[3];              // body acceleration; rho g joins the force (Sec. 4.1)
+    // density-dependent relaxation (var_visc): nu linear in rho from nu_l at
+    // visc_rl to nu_v at visc_rv, constant beyond; phi_sign = -1, or 0 with
+    // the correction off
+    int var_visc;
+    double nu_l, nu_v, visc_rv, visc_rl, phi_sign;
 };
+
+// Relaxation rate at density rho (the constant omega unless var_visc).
+__device__ __forceinline__ double omega_at(const Phys &p, double rho)
+{
+    if (!p.var_visc) return p.omega;
+    const double t = fmin(fmax((p.visc_rl - rho) / (p.visc_rl - p.visc_rv), 0.0), 1.0);
+    return 1.0 / (3.0 * (p.nu_l + (p.nu_v - p.nu_l) * t) + 0.5);
+}
 
 template <int LAT> struct Lattice;
 template <> struct Lattice<0> { static constexpr int D = 2, Q = 9; };
@@ -207,18 +220,20 @@ __global__ void k_collide(Geo g, Phys p, const uint8_t *__restrict__ mask,
     const double rho = c.x;
     double F[3] = {0.0, 0.0, 0.0};
     korteweg_force<LAT>(g, p, rp, x, y, z, rho, c.y, F);
-    // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2
+    // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2, the node's omega
+    const double om = omega_at(p, rho);
+    const double pref = p.var_visc ? p.phi_sign * (1.0 - 0.5 * om) : p.phi_pref;
     const int xm = wrapm(x - 1, g.nx), xp = wrapp(x + 1, g.nx);
     const int ym = wrapm(y - 1, g.ny), yp = wrapp(y + 1, g.ny);
     double Phi[3];
-    Phi[0] = p.phi_pref * 0.5 * (gflux[xp + g.nx * (y + g.ny * z)] - gflux[xm + g.nx * (y + g.ny * z)]);
-    Phi[1] = p.phi_pref * 0.5 * (gflux[g.N + x + g.nx * (yp + g.ny * z)] -
+    Phi[0] = pref * 0.5 * (gflux[xp + g.nx * (y + g.ny * z)] - gflux[xm + g.nx * (y + g.ny * z)]);
+    Phi[1] = pref * 0.5 * (gflux[g.N + x + g.nx * (yp + g.ny * z)] -
                                  gflux[g.N + x + g.nx * (ym + g.ny * z)]);
     int zm = 0, zp = 0;
     if (D == 3) {
         zm = wrapm(z - 1, g.nz);
         zp = wrapp(z + 1, g.nz);
-        Phi[2] = p.phi_pref * 0.5 * (gflux[2 * g.N + x + g.nx * (y + g.ny * zp)] -
+        Phi[2] = pref * 0.5 * (gflux[2 * g.N + x + g.nx * (y + g.ny * zp)] -
                                      gflux[2 * g.N + x + g.nx * (y + g.ny * zm)]);
     }
     // Product-form factors: equilibrium (xi = u, zeta = 1/3 + u^2) and
@@ -240,7 +255,7 @@ __global__ void k_collide(Geo g, Phys p, const uint8_t *__restrict__ mask,
     }
     const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
     // post = f* + (1 - omega)(f - feq); feq and f* by x-y partial products
-    const double omw = 1.0 - p.omega;
+    const double omw = 1.0 - om;
     double Ae[3][3], As[3][3];
 #pragma unroll
     for (int cx = 0; cx < 3; ++cx) {

@@ -26,7 +26,7 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 class lbm_params(C.Structure):
     _fields_ = [("a", C.c_double), ("b", C.c_double), ("acentric", C.c_double),
                 ("rho_w", C.c_double), ("storage", C.c_int), ("flags", C.c_int),
-                ("g", C.c_double * 3)]
+                ("g", C.c_double * 3), ("tau_v", C.c_double), ("visc_rho", C.c_double * 2)]
 
 
 class LBMError(RuntimeError):
@@ -132,7 +132,8 @@ class LBM:
                  kappa: float, tau: float, mask=None, a: float | None = None,
                  b: float | None = None, acentric: float | None = None,
                  rho_w: float | None = None, flags: int = 0, storage: int = F64,
-                 stream=None, torch_memory: bool = True, g=None):
+                 stream=None, torch_memory: bool = True, g=None, tau_v: float = 0.0,
+                 visc_rho=None):
         import torch
         self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, nz
         self.D = 2 if lattice == D2Q9 else 3
@@ -152,6 +153,9 @@ class LBM:
         if g is not None:   # body acceleration (gx, gy[, gz])
             for a, v in enumerate(g):
                 p.g[a] = float(v)
+        if tau_v:   # density-dependent relaxation between visc_rho = (rho_v, rho_l)
+            p.tau_v = float(tau_v)
+            p.visc_rho[0], p.visc_rho[1] = map(float, visc_rho)
         self.params = p
         mptr = None
         if mask is not None:

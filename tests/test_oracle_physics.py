@@ -349,3 +349,63 @@ def test_flat_interface_pressure_tensor():
     sigma = np.sum(P[0] - P[1]) / 2
     sigma_int = (kap * np.sum(np.gradient(rho) ** 2) + np.sum(rho * ux ** 2)) / 2
     assert sigma == pytest.approx(sigma_int, rel=0.01)
+
+
+@pytest.mark.parametrize("phase", ["vapour", "liquid"])
+def test_density_dependent_viscosity_in_each_phase(phase):
+    """With tau_v set, a uniform vapour (below rho_v) flows with the vapour
+    viscosity (tau_v) and a uniform liquid (above rho_l) with the liquid one
+    (tau): single-phase Poiseuille between halfway walls against
+    g y'(H - y') / (2 nu) with that phase's nu."""
+    e = EOS(0, 0.8, a=A_VDW)
+    rv, rl, _ = ph.maxwell(e)
+    rho0, tau, tau_v = (0.5, 0.8, 1.0) if phase == "vapour" else (7.2, 0.8, 1.0)
+    nu = ((tau_v if phase == "vapour" else tau) - 0.5) / 3.0
+    nx, ny, g = 5, 34, 1e-6
+    H = ny - 2
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = mask[-1] = 1
+    o = OracleLBM(0, nx, ny, 1, 0, 0.8, 0.0, tau, mask=mask.ravel(), a=A_VDW, rho_w=rho0,
+                  g=(g, 0.0), tau_v=tau_v, visc_rho=(rv, rl))
+    o.init(np.full(nx * ny, rho0))
+    o.step(int(6 * H * H / nu))
+    U = o.moments()[2][: nx * ny].reshape(ny, nx)[1:-1, 2]
+    yp = np.arange(1, ny - 1) - 0.5
+    ua = g / (2 * nu) * yp * (H - yp)
+    assert np.max(np.abs(U - ua)) < 2e-3 * ua.max()
+
+
+def test_layered_channel_with_viscosity_ratio_on_the_oracle():
+    """Sec. 4.1 configuration (b) scaled down: vdW T/Tc 0.36 (density ratio
+    1.2e3), dynamic viscosity ratio mu_l / mu_v = 11.3, so the vapour's
+    kinematic viscosity is 109 times the liquid's (tau 0.52 and 2.68). In a
+    40-row channel the steady velocity follows the momentum balance of the
+    simulated density and viscosity profile within 3 %."""
+    tr, H, tau_l, grav = 0.36, 40, 0.52, 1e-6
+    a0 = 9 / 49
+    e0 = EOS(0, tr, a=a0)
+    _, rl0, _ = ph.maxwell(e0)
+    h = 1e-6 * rl0
+    a = a0 * min(1.0, 0.1 / ((e0(rl0 + h) - e0(rl0 - h)) / (2 * h)))
+    e = EOS(0, tr, a=a)
+    rv, rl, ps = ph.maxwell(e)
+    kap = ph.kappa_for_width(e, 5.0, (rv, rl, ps))
+    nu_l = (tau_l - 0.5) / 3.0
+    nu_v = nu_l * (rl / rv) / 11.3
+    nx, ny, hl = 5, H + 2, H // 4
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = mask[-1] = 1
+    yp = np.arange(ny) - 0.5
+    from paper_2112_01975_gb300.inputs import tanh_interface
+    rho = np.repeat(tanh_interface(np.minimum(yp, H - yp) - hl, rl, rv, 5.0), nx)
+    rho[mask.ravel() == 1] = rl
+    o = OracleLBM(0, nx, ny, 1, 0, tr, kap, tau_l, mask=mask.ravel(), a=a, rho_w=rl,
+                  g=(grav, 0.0), tau_v=0.5 + 3 * nu_v, visc_rho=(rv, rl))
+    o.init(rho)
+    o.step(int(2 * hl * hl / nu_l))
+    r, _, U, _ = o.moments()
+    rr = r.reshape(ny, nx)[1:-1, 2]
+    Ux = U[: o.N].reshape(ny, nx)[1:-1, 2]
+    nu = nu_l + (nu_v - nu_l) * np.clip((rl - rr) / (rl - rv), 0.0, 1.0)
+    Ud = ph.channel_flow_from_profile(rr, grav, nu)
+    assert np.max(np.abs(Ux - Ud)) < 0.03 * Ud.max()
