@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -59,8 +61,11 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
-    ap.add_argument("--mode", default="step", choices=["step", "serve"],
-                    help="serve: the parameter-sweep server against one-at-a-time FP64")
+    ap.add_argument("--mode", default="step", choices=["step", "serve", "validate"],
+                    help="serve: the parameter-sweep server against one-at-a-time FP64; "
+                         "validate: the coexistence/Laplace, coalescence and impact runs "
+                         "at their configured lengths")
+    ap.add_argument("--validate", default="", help="validate mode: comma list of cfg2,cfg3,cfg4")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--request-steps", type=int, default=500)
     return ap.parse_args()
@@ -256,10 +261,153 @@ def run_serve(args):
         "data": "synthetic"}), flush=True)
 
 
+def _validate_cfg2(L, storage, tr, steps):
+    """D3Q27 128^3, PR at T/Tc: a flat slab (liquid 32 <= x < 96) for the
+    coexistence densities against Maxwell and the tension from the discrete
+    pressure tensor, and a drop of radius 24 for the Laplace law
+    Delta P = 2 sigma / R_e (3D), R_e the equimolar radius."""
+    from paper_2112_01975_gb300 import eos_tables, inputs
+    a = eos_tables.stable_a(1, tr)
+    rv, rl, ps = eos_tables.coexistence(1, tr, a)
+    kap = eos_tables.kappa_for_width(1, tr, a, width=5.0)
+    P = eos_tables.pressure(1, tr, a)
+    n = 128
+    st = {"f64": L.F64, "f32": L.F32}[storage]
+    g = L.LBM(1, n, n, n, 1, tr, kap, 1.0, a=a, storage=st)
+    g.init(inputs.slab(n, n, n, 32, 96, rv, rl))
+    t0 = time.perf_counter()
+    g.step(steps)
+    g.sync()
+    t_slab = time.perf_counter() - t0
+    rho = g.moments()[0].reshape(n, n, n)
+    line = rho[n // 2, n // 2]
+    Pt = g.pressure_tensor().reshape(6, n, n, n)[:, n // 2, n // 2]
+    sigma_flat = float(np.sum(Pt[0] - Pt[1])) / 2.0
+    g.close()
+    g = L.LBM(1, n, n, n, 1, tr, kap, 1.0, a=a, storage=st)
+    g.init(inputs.drop(n, n, n, 24.0, rv, rl))
+    g.step(steps)
+    rho = g.moments()[0].reshape(n, n, n)
+    r_in, r_out = float(rho[n // 2, n // 2, n // 2]), float(rho[0, 0, 0])
+    vol = (float(rho.sum()) - r_out * n ** 3) / (r_in - r_out)
+    R_e = (3.0 * vol / (4.0 * np.pi)) ** (1.0 / 3.0)
+    sigma_lap = float(P(r_in) - P(r_out)) * R_e / 2.0
+    g.close()
+    return {"T/Tc": tr, "storage": storage, "steps": steps, "rho_v": float(line[0]),
+            "rho_l": float(line[64]), "rho_v_maxwell": rv, "rho_l_maxwell": rl,
+            "rho_v_err": float(line[0]) / rv - 1.0, "rho_l_err": float(line[64]) / rl - 1.0,
+            "sigma_flat_pressure_tensor": sigma_flat, "sigma_laplace": sigma_lap,
+            "R_e": R_e, "laplace_vs_flat": sigma_lap / sigma_flat - 1.0,
+            "mlups_slab": n ** 3 * steps / t_slab / 1e6}
+
+
+def _validate_cfg3(L, torch, storage, steps, every=1000):
+    """Two PR drops of radius 40 touching at the centre of a periodic 256^3
+    box, T/Tc 0.45, tau 0.725: mass drift, far-field vapour and drop-centre
+    liquid densities, and the neck radius (liquid area of the mid-plane
+    between the drops, r = sqrt(A / pi)) every `every` steps."""
+    from paper_2112_01975_gb300 import eos_tables, inputs
+    tr, n, R = 0.45, 256, 40.0
+    a = eos_tables.stable_a(1, tr)
+    rv, rl, _ = eos_tables.coexistence(1, tr, a)
+    kap = eos_tables.kappa_for_width(1, tr, a, width=5.0)
+    st = {"f64": L.F64, "f32": L.F32, "f16s": L.F16S, "bf16s": L.BF16S}[storage]
+    centres = [(n // 2 - R, n // 2, n // 2), (n // 2 + R, n // 2, n // 2)]
+    rho0 = inputs.add_noise(inputs.drops(n, n, n, centres, R, rv, rl, width=5.0), 1e-4, 3)
+    g = L.LBM(1, n, n, n, 1, tr, kap, 0.725, a=a, storage=st)
+    g.init(rho0)
+    m0, _ = g.reduce()
+    rho_t = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+    mid = 0.5 * (rl + rv)
+    neck, t0 = [], time.perf_counter()
+    for s in range(every, steps + 1, every):
+        g.step(every)
+        g.moments((rho_t, None, None))
+        area = int((rho_t.view(n, n, n)[:, :, n // 2] > mid).sum())
+        neck.append((s, float(np.sqrt(area / np.pi))))
+    g.sync()
+    dt = time.perf_counter() - t0
+    m1, _ = g.reduce()
+    r = rho_t.view(n, n, n)
+    liquid = r[r > mid]
+    vapour = r[r < mid]
+    out = {"storage": storage, "steps": steps, "mass_drift": m1 / m0 - 1.0,
+           "rho_v_far": float(r[0, 0, 0]), "rho_l_median": float(liquid.median()),
+           "rho_v_median": float(vapour.median()), "rho_l_maxwell": rl, "rho_v_maxwell": rv,
+           "neck_radius": neck, "mlups_incl_readback": n ** 3 * steps / dt / 1e6}
+    g.close()
+    return out
+
+
+def _validate_cfg4(L, steps, every=2000):
+    """A PR drop of radius 60 moving down at U = 0.05 onto 8x8x16 pillars
+    (pitch 16) on a wall, 384x384x256, T/Tc 0.5, tau 0.725, FP32: mass
+    drift, the liquid area just above the pillar tops and the height of the
+    liquid's centre of mass over time, and the last step reached."""
+    from paper_2112_01975_gb300 import eos_tables, inputs
+    tr, (nx, ny, nz), R, U = 0.5, (384, 384, 256), 60.0, 0.05
+    a = eos_tables.stable_a(1, tr)
+    rv, rl, _ = eos_tables.coexistence(1, tr, a)
+    kap = eos_tables.kappa_for_width(1, tr, a, width=5.0)
+    mask = inputs.pillar_mask(nx, ny, nz, seed=4)
+    drop = inputs.drop(nx, ny, nz, R, rv, rl, width=5.0, center=(nx // 2, ny // 2, 16 + R + 8))
+    u0 = np.zeros(3 * drop.size)
+    u0[2 * drop.size:] = np.where(mask == 1, 0.0, -U * (drop - rv) / (rl - rv))
+    g = L.LBM(1, nx, ny, nz, 1, tr, kap, 0.725, mask=mask, a=a, rho_w=rv, storage=L.F32)
+    g.init(np.where(mask == 1, rv, drop), u0)
+    m0, _ = g.reduce()
+    wet, t0, failed = [], time.perf_counter(), None
+    for s in range(every, steps + 1, every):
+        g.step(every)
+        try:
+            rho = g.moments()[0].reshape(nz, ny, nx)
+        except L.LBMError as exc:
+            failed = f"step <= {s}: {exc}"
+            break
+        liq = rho > 0.5 * (rl + rv)
+        zc = float((np.arange(nz)[:, None, None] * liq).sum() / max(liq.sum(), 1))
+        wet.append((s, float(np.sqrt(np.count_nonzero(liq[17]) / np.pi)), zc))
+    dt = time.perf_counter() - t0
+    out = {"steps": steps, "step_wetted_radius_z17_liquid_z": wet, "failed": failed}
+    if failed is None:
+        m1, _ = g.reduce()
+        out["mass_drift"] = m1 / m0 - 1.0
+        out["mlups_incl_readback"] = nx * ny * nz * steps / dt / 1e6
+    g.close()
+    return out
+
+
+def run_validate(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    from paper_2112_01975_gb300 import lbm as L
+    torch.cuda.set_device(0)
+    res = {"mode": "validate", "data": "synthetic", "cfg2": [], "cfg3": [], "cfg4": None}
+    only = set(args.validate.split(",")) if args.validate else {"cfg2", "cfg3", "cfg4"}
+    for tr in (0.9, 0.7) if "cfg2" in only else ():
+        for st in ("f64", "f32"):
+            res["cfg2"].append(_validate_cfg2(L, st, tr, 20000))
+            print(json.dumps(res["cfg2"][-1]), file=sys.stderr, flush=True)
+    for st in ("f64", "f32", "f16s", "bf16s") if "cfg3" in only else ():
+        res["cfg3"].append(_validate_cfg3(L, torch, st, 10000))
+        print(json.dumps(res["cfg3"][-1]), file=sys.stderr, flush=True)
+    ref = res["cfg3"][0] if res["cfg3"] else None
+    for r in res["cfg3"][1:]:
+        for k in ("rho_v_far", "rho_l_median", "rho_v_median"):
+            r[k + "_vs_f64"] = r[k] / ref[k] - 1.0
+    if "cfg4" in only:
+        res["cfg4"] = _validate_cfg4(L, 20000, every=1000)
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "validate":
+        run_validate(args)
         return
     from paper_2112_01975_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
