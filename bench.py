@@ -66,6 +66,8 @@ def parse():
                          "validate: the coexistence/Laplace, coalescence and impact runs "
                          "at their configured lengths")
     ap.add_argument("--validate", default="", help="validate mode: comma list of cfg2,cfg3,cfg4")
+    ap.add_argument("--validate-storages", default="f64,f32,f16s,bf16s",
+                    help="validate mode: storages of the coalescence run")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--request-steps", type=int, default=500)
     return ap.parse_args()
@@ -389,11 +391,11 @@ def run_validate(args):
         for st in ("f64", "f32"):
             res["cfg2"].append(_validate_cfg2(L, st, tr, 20000))
             print(json.dumps(res["cfg2"][-1]), file=sys.stderr, flush=True)
-    for st in ("f64", "f32", "f16s", "bf16s") if "cfg3" in only else ():
+    for st in args.validate_storages.split(",") if "cfg3" in only else ():
         res["cfg3"].append(_validate_cfg3(L, torch, st, 10000))
         print(json.dumps(res["cfg3"][-1]), file=sys.stderr, flush=True)
-    ref = res["cfg3"][0] if res["cfg3"] else None
-    for r in res["cfg3"][1:]:
+    ref = res["cfg3"][0] if res["cfg3"] and res["cfg3"][0]["storage"] == "f64" else None
+    for r in (res["cfg3"][1:] if ref else []):
         for k in ("rho_v_far", "rho_l_median", "rho_v_median"):
             r[k + "_vs_f64"] = r[k] / ref[k] - 1.0
     if "cfg4" in only:

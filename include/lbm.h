@@ -72,9 +72,10 @@ enum lbm_eos {
 /* Population storage. LBM_F64 stores and computes in FP64 (two kernels per
  * step). LBM_F32 stores populations in FP32 and runs the step as one fused
  * FP32 kernel. LBM_F16S / LBM_BF16S store each population as the 16-bit
- * (FP16 / BF16) deviation h_i = f_i - w_i rho(src) from the weight times the
- * FP32 density of the node that pushed it (the node itself after a
- * bounce-back), with an FP32 density field beside each buffer; the fused
+ * (FP16 / BF16) relative deviation h_i = f_i / rho(src) - w_i from the
+ * weight, rho(src) the FP32 density of the node that pushed it (the node
+ * itself after a bounce-back), with an FP32 density field beside each
+ * buffer; the fused
  * step computes in FP32; lattices with solid nodes are refused. Moments,
  * reductions and population I/O are FP64 at the ABI for every storage. */
 enum lbm_storage { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 };

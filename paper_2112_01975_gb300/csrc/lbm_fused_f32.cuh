@@ -20,9 +20,11 @@
 
 namespace lbmf {
 
-// Storage of populations: float (FP32), or 16-bit values of the shift
-// h_i = f_i - w_i rho(src) with rho(src) the FP32 density of the node that
-// pushed the population (the node itself after a bounce-back).
+// Storage of populations: float (FP32), or 16-bit values of the relative
+// shift h_i = f_i / rho(src) - w_i, with rho(src) the FP32 density of the node
+// that pushed the population (the node itself after a bounce-back). Relative
+// to the source density, h stays O(1e-3) in a vapour of any density, where
+// the absolute shift f_i - w_i rho would fall below FP16's normal range.
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -155,7 +157,7 @@ __device__ __forceinline__ float decode_pop(ST hv, int i, int r, int c, int q, c
     if constexpr (IsShifted<ST>::value) {
         using L = LatF<LAT>;
         const int rr = r + (LAT == 1 ? 1 : 0) - L::cy(i), cc = c + 1 - L::cx(i);
-        return to_f(hv) + weight_f<LAT>(i) * sm.rs[(q - L::cz(i) + SM::QS) & (SM::QS - 1)][rr][cc];
+        return (weight_f<LAT>(i) + to_f(hv)) * sm.rs[(q - L::cz(i) + SM::QS) & (SM::QS - 1)][rr][cc];
     } else {
         return to_f(hv);
     }
@@ -436,7 +438,7 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
                     const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
-                    const float post = SHIFT ? fmaf(omw, fi[i] - es.x, es.y) - weight_f<LAT>(i) * rho
+                    const float post = SHIFT ? fmaf(fmaf(omw, fi[i] - es.x, es.y), inv, -weight_f<LAT>(i))
                                              : fmaf(omw, fi[i] - es.x, es.y);
                     const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
                                          plane * (unsigned)Z[cz + 1];

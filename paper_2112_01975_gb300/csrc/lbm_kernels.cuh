@@ -514,7 +514,7 @@ k_reduce_final(const double *__restrict__ partial, double *__restrict__ out)
     }
 }
 
-// Shifted 16-bit storage (h_i = f_i - w_i rho(src), src = r - c_i, or r itself
+// Shifted 16-bit storage (h_i = f_i / rho(src) - w_i, src = r - c_i, or r itself
 // when r - c_i is solid): decode to FP64, per-node densities, encode.
 __device__ __forceinline__ double weight_d(int i, int D)
 {
@@ -540,8 +540,8 @@ __global__ void k_decode_shifted(Geo g, const ST *__restrict__ h, const float *_
     const unsigned n = x + g.nx * (y + g.ny * z);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        f[(size_t)i * g.N + n] = (double)lbmf::to_f(h[(size_t)i * g.N + n]) +
-                                 weight_d(i, D) * (double)rho_src[source_node(g, D, i, x, y, z)];
+        f[(size_t)i * g.N + n] = (weight_d(i, D) + (double)lbmf::to_f(h[(size_t)i * g.N + n])) *
+                                 (double)rho_src[source_node(g, D, i, x, y, z)];
 }
 
 template <int LAT>
@@ -569,7 +569,7 @@ __global__ void k_encode_shifted(Geo g, const double *__restrict__ f, const floa
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         h[(size_t)i * g.N + n] = lbmf::from_f<ST>(
-            (float)(f[(size_t)i * g.N + n] - weight_d(i, D) * (double)rho[source_node(g, D, i, x, y, z)]));
+            (float)(f[(size_t)i * g.N + n] / (double)rho[source_node(g, D, i, x, y, z)] - weight_d(i, D)));
 }
 
 // Element-wise type conversion (population I/O of FP32 storage).

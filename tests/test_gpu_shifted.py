@@ -1,9 +1,10 @@
-"""16-bit shifted storage (FP16 / BF16 deviations h_i = f_i - w_i rho(src)
-from the weight times the pushing node's FP32 density), FP32 arithmetic,
+"""16-bit shifted storage (FP16 / BF16 relative deviations
+h_i = f_i / rho(src) - w_i from the weight, rho(src) the pushing node's FP32
+density), FP32 arithmetic,
 against the FP64 oracle. The stated accuracy of 16-bit storage is
 coexistence densities within 2 % of FP64; nodes are compared at that
 tolerance after 1000 steps, and one step from an identical state at the
-16-bit rounding of h (|h| <~ 0.1 w rho: 5e-5 of max f for FP16, 4e-4 for
+16-bit rounding of h (|h| <~ 0.1 w: 5e-5 of max f for FP16, 4e-4 for
 BF16, with margin)."""
 import numpy as np
 import pytest
