@@ -173,6 +173,21 @@ int lbm_step(lbm_handle h, int64_t n);
  * nodes report rho_w and zero velocities. Synchronises the stream. */
 int lbm_moments(lbm_handle h, double *rho, double *u, double *U, int on_device);
 
+/* Interpolated bounce-back for curved or off-grid walls (the linear scheme of
+ * Bouzidi, Firdaouss and Lallemand that the paper uses for curved solids,
+ * Sec. 4.5). q: host double[Q * N], component-major (q[i * N + n]): for a
+ * link from fluid node n along c_i into a solid node, the wall sits at the
+ * fraction q in (0, 1] of the link; entries <= 0, entries of other links,
+ * and links whose node n - c_i is solid keep halfway bounce-back (q = 1/2
+ * is halfway exactly). Each step then rewrites the populations bounced at
+ * such links by interpolation and returns each boundary node's net change
+ * through its rest population, so the walls conserve mass (without that
+ * the interpolation's mass defect grows at walls under the non-ideal force).
+ * NULL clears. Copies what it needs to device memory it allocates (freed by
+ * lbm_destroy); synchronises. LBM_EINVAL for q > 1. Lattices with such walls
+ * cannot join a batch. */
+int lbm_set_wall_distances(lbm_handle h, const double *q);
+
 /* Discrete pressure tensor of the current state (Appendix E): at each fluid
  * node the populations' momentum flux sum_i c_ia c_ib f_i plus the non-local
  * contributions of the four ring terms of the force (Eq. Kforce_final), with

@@ -70,6 +70,7 @@ def lib(openmp: bool = False):
         L.oracle_eos_alpha.argtypes = [C.c_int, C.c_double, C.c_double]
         L.oracle_pressure_tensor.argtypes = [C.c_void_p, _dp]
         L.oracle_set_viscosity.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]
+        L.oracle_set_wall_distances.argtypes = [C.c_void_p, C.c_void_p]
         L.oracle_eos_pressure_array.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                                                 C.c_double, _dp, C.c_long, _dp]
         _libs[openmp] = L
@@ -214,6 +215,15 @@ class OracleLBM:
         out = np.empty(self.Q)
         self._L.oracle_post_local(self._h, _p(b), m.ctypes.data_as(C.c_void_p), _p(out))
         return out
+
+    def set_wall_distances(self, q):
+        """Wall distance q[i][n] in (0, 1] of each link from node n along c_i
+        into a solid (interpolated bounce-back); None: halfway everywhere."""
+        if q is None:
+            self._L.oracle_set_wall_distances(self._h, None)
+            return
+        self._qw = np.ascontiguousarray(q, dtype=np.float64).reshape(self.Q * self.N)
+        self._L.oracle_set_wall_distances(self._h, self._qw.ctypes.data_as(C.c_void_p))
 
     def pressure_tensor(self) -> np.ndarray:
         """Discrete pressure tensor (Appendix E): [component][node] with the

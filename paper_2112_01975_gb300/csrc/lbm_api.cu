@@ -46,6 +46,10 @@ struct lbm_ctx {
     bool initialised = false, bad = false;
     cudaGraphExec_t graph = nullptr;
     int64_t launches = 0;
+    // interpolated bounce-back: boundary nodes, their active links, wall distances
+    int nb = 0;
+    unsigned *bn = nullptr, *bmask = nullptr;
+    double *bq = nullptr;
     char err[512] = {0};
 };
 
@@ -268,6 +272,16 @@ int launch_step(lbm_ctx *h, cudaStream_t s, int *nk)
                                                h->gflux);
         *nk = 2;
     }
+    if (h->nb > 0) {   // interpolated bounce-back on the new state
+        const int th = 128, bl = (h->nb + th - 1) / th;
+        if (h->storage == LBM_F32)
+            lbmk::k_interp_bounce_back<LAT, float><<<bl, th, 0, s>>>(h->geo, h->bn, h->bmask, h->bq,
+                                                                     h->nb, f32(h, h->cur ^ 1));
+        else
+            lbmk::k_interp_bounce_back<LAT, double><<<bl, th, 0, s>>>(h->geo, h->bn, h->bmask, h->bq,
+                                                                      h->nb, f64(h, h->cur ^ 1));
+        *nk += 1;
+    }
     CU(h, cudaGetLastError());
     h->cur ^= 1;
     return LBM_OK;
@@ -282,7 +296,7 @@ int step_plain(lbm_ctx *h, cudaStream_t s, int *nk_out = nullptr)
     return rc;
 }
 
-int kernels_per_step(const lbm_ctx *h) { return h->storage == LBM_F64 ? 2 : 1; }
+int kernels_per_step(const lbm_ctx *h) { return (h->storage == LBM_F64 ? 2 : 1) + (h->nb > 0); }
 
 // Shifted storage I/O goes through a temporary FP64 copy of the populations.
 struct TempF64 {
@@ -752,6 +766,64 @@ int lbm_moments(lbm_handle h, double *rho, double *u, double *U, int on_device)
     return read_status(h);
 }
 
+int lbm_set_wall_distances(lbm_handle h, const double *q)
+{
+    if (!h) return LBM_EINVAL;
+    const size_t N = h->geo.N;
+    const int Q = h->Q, D = h->D;
+    const Geo &g = h->geo;
+    std::vector<unsigned> bn, bm;
+    std::vector<double> bq;
+    if (q) {
+        for (size_t n = 0; n < N; ++n) {
+            if (h->mask_host[n]) continue;
+            const int x = n % g.nx, y = (n / g.nx) % g.ny, z = n / ((size_t)g.nx * g.ny);
+            unsigned m = 0;
+            double qq[27] = {0.0};
+            for (int i = 0; i < Q; ++i) {
+                const int c[3] = {i % 3 - 1, (i / 3) % 3 - 1, D == 3 ? i / 9 - 1 : 0};
+                const size_t nd = (size_t)((x + c[0] + g.nx) % g.nx) +
+                                  (size_t)g.nx * (((y + c[1] + g.ny) % g.ny) +
+                                                  (size_t)g.ny * ((z + c[2] + g.nz) % g.nz));
+                const size_t nm = (size_t)((x - c[0] + g.nx) % g.nx) +
+                                  (size_t)g.nx * (((y - c[1] + g.ny) % g.ny) +
+                                                  (size_t)g.ny * ((z - c[2] + g.nz) % g.nz));
+                const double qi = q[(size_t)i * N + n];
+                if (!h->mask_host[nd] || !(qi > 0.0)) continue;
+                if (!(qi <= 1.0)) return fail(h, LBM_EINVAL, "wall distance q > 1 at node %zu", n);
+                if (h->mask_host[nm]) continue;   // no fluid node behind: stays halfway
+                m |= 1u << i;
+                qq[i] = qi;
+            }
+            if (m) {
+                bn.push_back((unsigned)n);
+                bm.push_back(m);
+                bq.insert(bq.end(), qq, qq + Q);
+            }
+        }
+    }
+    if (h->stream) CU(h, cudaStreamSynchronize(h->stream));
+    if (h->bn) cudaFree(h->bn);
+    if (h->bmask) cudaFree(h->bmask);
+    if (h->bq) cudaFree(h->bq);
+    h->bn = h->bmask = nullptr;
+    h->bq = nullptr;
+    h->nb = 0;
+    if (h->graph) {   // the captured steps change
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (bn.empty()) return LBM_OK;
+    CU(h, cudaMalloc(&h->bn, sizeof(unsigned) * bn.size()));
+    CU(h, cudaMalloc(&h->bmask, sizeof(unsigned) * bm.size()));
+    CU(h, cudaMalloc(&h->bq, sizeof(double) * bq.size()));
+    CU(h, cudaMemcpy(h->bn, bn.data(), sizeof(unsigned) * bn.size(), cudaMemcpyHostToDevice));
+    CU(h, cudaMemcpy(h->bmask, bm.data(), sizeof(unsigned) * bm.size(), cudaMemcpyHostToDevice));
+    CU(h, cudaMemcpy(h->bq, bq.data(), sizeof(double) * bq.size(), cudaMemcpyHostToDevice));
+    h->nb = (int)bn.size();
+    return LBM_OK;
+}
+
 int lbm_pressure_tensor(lbm_handle h, double *P, int on_device)
 {
     int rc = check_ready(h);
@@ -967,7 +1039,8 @@ int lbm_batch_create(lbm_batch *out, const lbm_handle *members, int count)
     if (storage == LBM_F64) return LBM_EINVAL;
     for (int k = 0; k < count; ++k) {
         lbm_ctx *h = members[k];
-        if (!h || !h->initialised || h->bad || h->storage != storage || h->lattice != lattice)
+        if (!h || !h->initialised || h->bad || h->storage != storage || h->lattice != lattice ||
+            h->nb > 0)   // interpolated bounce-back is not part of the batched step
             return LBM_EINVAL;
         for (int j = 0; j < k; ++j)
             if (members[j] == h) return LBM_EINVAL;   // a lattice at most once
@@ -1241,6 +1314,9 @@ void lbm_destroy(lbm_handle h)
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->owns_base && h->base) cudaFree(h->base);
+    if (h->bn) cudaFree(h->bn);
+    if (h->bmask) cudaFree(h->bmask);
+    if (h->bq) cudaFree(h->bq);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     cudaGetLastError();
     delete h;

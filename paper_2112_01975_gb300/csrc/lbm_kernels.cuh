@@ -310,6 +310,47 @@ __global__ void k_moments_out(Geo g, Phys p, const uint8_t *__restrict__ mask,
     }
 }
 
+// Interpolated (linear Bouzidi) bounce-back, after a push step with halfway
+// bounce-back, one boundary node per thread. For each active link of node n
+// along c_i into a solid, with the wall at the fraction q of the link
+// (ib = Q-1-i; f_ib(n) holds f_i*(n), f_i(n) holds f_i*(n - c_i),
+// f_ib(n - c_i) holds f_ib*(n)):
+//   q < 1/2:  f_ib(n) = 2q f_i*(n) + (1 - 2q) f_i*(n - c_i)
+//   q >= 1/2: f_ib(n) = f_i*(n) / (2q) + (2q - 1)/(2q) f_ib*(n)
+// and the node returns the sum of its links' changes through its rest
+// population (mass-conserving). Active links have n - c_i fluid, so no
+// thread reads what another writes.
+template <int LAT, typename T>
+__global__ void k_interp_bounce_back(Geo g, const unsigned *__restrict__ bn,
+                                     const unsigned *__restrict__ bmask,
+                                     const double *__restrict__ bq, int nb, T *__restrict__ f)
+{
+    constexpr int D = Lattice<LAT>::D, Q = Lattice<LAT>::Q;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const unsigned n = bn[b], m = bmask[b];
+    const int x = n % g.nx, y = (n / g.nx) % g.ny, z = n / (g.nx * g.ny);
+    T excess = T(0);
+    for (int i = 0; i < Q; ++i) {
+        if (!((m >> i) & 1u)) continue;
+        const T q = (T)bq[(size_t)b * Q + i];
+        const int ib = Q - 1 - i;
+        const T a = f[(size_t)ib * g.N + n];
+        T v;
+        if (q < T(0.5)) {
+            v = T(2) * q * a + (T(1) - T(2) * q) * f[(size_t)i * g.N + n];
+        } else {
+            const int xm = (x - cxi(i) + g.nx) % g.nx, ym = (y - cyi(i) + g.ny) % g.ny;
+            const int zm = D == 3 ? (z - czi(i) + g.nz) % g.nz : 0;
+            const unsigned nm = xm + g.nx * (ym + g.ny * zm);
+            v = a / (T(2) * q) + (T(2) * q - T(1)) / (T(2) * q) * f[(size_t)ib * g.N + nm];
+        }
+        f[(size_t)ib * g.N + n] = v;
+        excess += v - a;
+    }
+    f[(size_t)(Q / 2) * g.N + n] -= excess;
+}
+
 // Discrete pressure tensor (Appendix E) at fluid nodes: the populations'
 // momentum flux sum_i c_ia c_ib f_i plus the non-local parts of the four
 // ring terms of the force, with the sign of the force on the fluid:

@@ -53,6 +53,7 @@ def _load():
     L.lbm_moments.argtypes = [vp, vp, vp, vp, C.c_int]
     L.lbm_reduce.argtypes = [vp, dp, dp]
     L.lbm_pressure_tensor.argtypes = [vp, vp, C.c_int]
+    L.lbm_set_wall_distances.argtypes = [vp, vp]
     L.lbm_get_populations.argtypes = [vp, vp, C.c_int]
     L.lbm_set_populations.argtypes = [vp, vp, C.c_int]
     L.lbm_sync.argtypes = [vp, C.c_int]
@@ -222,6 +223,17 @@ class LBM:
         rho, u, U = out
         self._check(_lib.lbm_moments(self._h, *(None if t is None else _ptr(t) for t in out), 1))
         return rho, u, U
+
+    def set_wall_distances(self, q):
+        """Wall distance q[i][n] in (0, 1] of the links from fluid node n
+        along c_i into a solid (interpolated bounce-back); None clears."""
+        if q is None:
+            self._check(_lib.lbm_set_wall_distances(self._h, None))
+            return
+        qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+        if qq.size != self.Q * self.N:
+            raise ValueError("q needs Q * N entries")
+        self._check(_lib.lbm_set_wall_distances(self._h, qq.ctypes.data))
 
     def pressure_tensor(self, out=None):
         """Discrete pressure tensor [component][node] (xx, yy[, zz], xy[, xz,
