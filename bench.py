@@ -454,9 +454,9 @@ def main():
     alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * w.nodes
     achieved = alg / (ms_collide * 1e-3) / 1e9
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
-    # fused step on this 128^3 workload (FP32: 260.5 + 188.2 MB; FP16
-    # shifted: 137.7 + 86.3 MB)
-    traffic_fused = {"f32": 448.79e6, "f16s": 223.93e6}.get(args.storage) \
+    # fused step on this 128^3 workload (FP32: 261.7 + 186.9 MB; FP16
+    # shifted: 137.7 + 81.7 MB)
+    traffic_fused = {"f32": 448.60e6, "f16s": 219.36e6}.get(args.storage) \
         if w.name == "d3q27_drop_128^3_pr_tr0.7" else None
     if storage != F64:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -469,7 +469,7 @@ def main():
         tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                    "traffic": 402.38e6 * w.nodes / 884736 if w.lattice == 1 else None,
+                    "traffic": 402.63e6 * w.nodes / 884736 if w.lattice == 1 else None,
                     "kernel": "k_collide (FP64)",
                     "peak_source": "nominal FP64 rate of GB300 (recipe table)",
                     "flops_per_node": COLLIDE_FP64_FLOPS_PER_NODE,
