@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -54,6 +55,19 @@ struct lbm_ctx {
 };
 
 namespace {
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory, once per
+// device (the attribute belongs to the device the call runs on).
+template <typename Kern>
+void smem_opt_in(Kern kernel, int bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done.fetch_or(bit);
+}
 
 constexpr size_t kAlign = 256;
 
@@ -232,13 +246,9 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 template <int LAT, typename ST>
 void launch_shifted_t(lbm_ctx *h, cudaStream_t s, int k)
 {
-    static bool attr_set = false;   // once per kernel instance per process
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
     const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
-    if (!attr_set) {
-        cudaFuncSetAttribute(lbmf::k_step_shifted<LAT, ST>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        attr_set = true;
-    }
+    smem_opt_in(lbmf::k_step_shifted<LAT, ST>, bytes, done);
     using L = lbmf::LatF<LAT>;
     lbmf::k_step_shifted<LAT, ST><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
         h->geof, h->physf, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
@@ -986,13 +996,9 @@ namespace {
 template <int LAT, typename ST>
 void launch_batch_shifted(lbm_batch_ctx *b, int parity, cudaStream_t s)
 {
-    static bool attr_set = false;   // once per kernel instance per process
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
     const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
-    if (!attr_set) {
-        cudaFuncSetAttribute(lbmf::k_step_shifted_batch<LAT, ST>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        attr_set = true;
-    }
+    smem_opt_in(lbmf::k_step_shifted_batch<LAT, ST>, bytes, done);
     lbmf::k_step_shifted_batch<LAT, ST>
         <<<b->grid, lbmf::LatF<LAT>::TX * lbmf::LatF<LAT>::TY, bytes, s>>>(
             b->d_members[parity], b->d_items, b->n_items);
