@@ -136,6 +136,21 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def host_cpu() -> dict:
+    """The host's CPU model (lscpu, else the platform) and core count."""
+    import platform
+    model = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu": model, "nproc": os.cpu_count()}
+
+
 def oracle_sample_mlups(w, target_s: float = 12.0, openmp: bool = False):
     """FP64 oracle throughput on a centred crop of the workload: one host
     thread, or (openmp) the -fopenmp build of the same source on all cores."""
@@ -461,6 +476,7 @@ def main():
     if storage != F64:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic_fused,
+                    "frac_of_nominal_7900_gbs": achieved / 7900.0,
                     "kernel": "k_step_f32 (fused step)" if storage == F32 else "k_step_shifted",
                     "peak_source": peak_kind + " hbm_gbs",
                     "alg_bytes_per_launch": alg, "ms_per_launch": ms_collide,
@@ -521,7 +537,8 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, sample = oracle_sample_mlups(w)
-        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
+               "host": host_cpu()}
         try:   # the same oracle built with -fopenmp, all host cores
             va, sa = oracle_sample_mlups(w, target_s=6.0, openmp=True)
             cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
