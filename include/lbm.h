@@ -126,7 +126,9 @@ int lbm_default_params(int eos, lbm_params *p);
 
 /* Create a handle for one lattice. lattice: enum lbm_lattice. nx, ny, nz:
  * lattice size, each >= 5 (the 2-ring stencils must not alias under the
- * periodic wrap); nz must be 1 for D2Q9. eos: enum lbm_eos. t_over_tc:
+ * periodic wrap); nz must be 1 for D2Q9; at most 4e9 / 27 nodes (about
+ * 148 million, e.g. 529^3: the kernels index populations with 32-bit
+ * integers), else LBM_EINVAL. eos: enum lbm_eos. t_over_tc:
  * reduced temperature, 0 < T/Tc < 1 (T = (T/Tc) Tc, Tc from a and b by the
  * relations printed under each EOS). kappa: capillary coefficient kappa~ of
  * Eq. capillary_discrete, >= 0. tau: relaxation time, omega = 1/tau, > 1/2

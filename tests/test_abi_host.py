@@ -51,6 +51,10 @@ def test_required_bytes(lib):
     assert n >= 2 * 27 * 8 * N + 16 * N + 2 * 3 * 8 * N + N
     assert n < 2 * 27 * 8 * N + 16 * N + 2 * 3 * 8 * N + N + 64 * 1024
     assert lib.lbm_required_bytes(0, 64, 64, 2, 0) == 0      # D2Q9 needs nz = 1
+    # the largest lattice: 27 N <= 4e9 (32-bit population indices)
+    assert lib.lbm_required_bytes(1, 529, 529, 529, 1) > 0
+    assert lib.lbm_required_bytes(1, 530, 530, 530, 1) == 0
+    assert lib.lbm_required_bytes(0, 20000, 8000, 1, 1) == 0
     assert lib.lbm_required_bytes(1, 4, 64, 64, 0) == 0      # below the 2-ring minimum
     assert lib.lbm_required_bytes(1, 64, 64, 64, 7) == 0     # unknown storage
 
