@@ -15,6 +15,7 @@ the paper's Sec. 6 and of Sec. 4.1 configuration (b)) on the GPU.
 import numpy as np
 import pytest
 
+from conftest import printed
 from oracle import physics as ph
 from oracle.lbm import EOS, OracleLBM
 from paper_2112_01975_gb300 import inputs
@@ -74,7 +75,7 @@ def test_layered_poiseuille_viscosity_ratio_200_rows(lbm):
     rv, rl, ps = ph.maxwell(e)
     kap = ph.kappa_for_width(e, 5.0, (rv, rl, ps))
     nu_l = (tau_l - 0.5) / 3.0
-    nu_v = nu_l * (rl / rv) / 11.3
+    nu_v = nu_l * (rl / rv) / printed("layered_poiseuille_b")["viscosity_ratio"]   # mu_l / mu_v
     nx, ny, hl = 5, H + 2, H // 4
     mask = np.zeros((ny, nx), np.uint8)
     mask[0] = mask[-1] = 1

@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+from conftest import printed
 from oracle import physics as ph
 from oracle.lbm import EOS
 from paper_2112_01975_gb300 import inputs
@@ -55,8 +56,9 @@ def test_shan_chen_critical_points(eos, gc, rc):
     at rho_c, and nowhere else does P' vanish."""
     e = EOS(eos, 1.0)
     assert e.RT == pytest.approx(gc, rel=1e-15)
-    assert round(rc, 4) == pytest.approx({4: 0.6931, 5: 1.0}[eos], abs=1e-12)
-    assert round(-gc, 3) == pytest.approx({4: 4.0, 5: 7.389}[eos], abs=1e-12)
+    pv = printed({4: "shan_chen_1_critical", 5: "shan_chen_2_critical"}[eos])
+    assert round(rc, 4) == pytest.approx(pv["rho_c"], abs=1e-12)        # as printed
+    assert round(gc, 3) == pytest.approx(pv["G_c"], abs=1e-12)
     d1, d2 = _d(e, rc)
     assert abs(d1) < 1e-7 and abs(d2) < 1e-5
     grid = np.linspace(0.05, 5.0, 4001)
@@ -105,8 +107,9 @@ def test_corresponding_states():
 def test_printed_density_ratio_tr077():
     """Sec. 4.1 quotes rho_l/rho_v = 10.1 at T_r = 0.77 for vdW (simulated);
     the equal-area ratio is within the paper's quoted deviations of it."""
-    rv, rl, _ = ph.maxwell(EOS(0, 0.77))
-    assert rl / rv == pytest.approx(10.1, rel=0.02)
+    pv = printed("layered_poiseuille_a")
+    rv, rl, _ = ph.maxwell(EOS(0, pv["T_r"]))
+    assert rl / rv == pytest.approx(pv["density_ratio"], rel=0.02)
 
 
 def test_surface_tension_near_critical_asymptote():

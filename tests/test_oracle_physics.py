@@ -17,6 +17,7 @@
 import numpy as np
 import pytest
 
+from conftest import printed
 from oracle import physics as ph
 from oracle.lbm import EOS, FORCE_PRINTED_SIGN, OracleLBM, PHI_OFF, PHI_PRINTED_SIGN
 from paper_2112_01975_gb300 import inputs
@@ -218,9 +219,15 @@ def _appendix_two_layer(y, H, hl, rl, rv, ml, mv, g, restore_bv=True):
     return np.where(y <= hl, al * y * y + bl * y, av * y * y + bv * y + cv)
 
 
-@pytest.mark.parametrize("case", [(200.0, 100.0, 10.1, 1.0, 10.1, 1.0),     # Sec. 4.1 (a)
-                                  (200.0, 70.0, 1030.0, 1.0, 11.3, 1.0),    # Sec. 4.1 (b)
-                                  (1.0, 0.3, 2.0, 5.0, 0.7, 3.0)])
+def _printed_cases():
+    a, b = printed("layered_poiseuille_a"), printed("layered_poiseuille_b")
+    H = float(printed("layered_poiseuille_grid")["ny"])
+    return [(H, H / 2, a["density_ratio"], 1.0, a["viscosity_ratio"], 1.0),       # Sec. 4.1 (a)
+            (H, 0.35 * H, b["density_ratio"], 1.0, b["viscosity_ratio"], 1.0),   # Sec. 4.1 (b)
+            (1.0, 0.3, 2.0, 5.0, 0.7, 3.0)]
+
+
+@pytest.mark.parametrize("case", _printed_cases())
 def test_layered_solver_against_the_two_layer_appendix_solution(case):
     """The layer solver satisfies the ODEs and interface conditions of Sec.
     4.1 and equals the appendix's two-layer closed form once b_v's dropped
