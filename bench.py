@@ -469,9 +469,9 @@ def main():
     alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * w.nodes
     achieved = alg / (ms_collide * 1e-3) / 1e9
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
-    # fused step on this 128^3 workload (FP32: 261.7 + 186.9 MB; FP16
-    # shifted: 137.7 + 81.7 MB)
-    traffic_fused = {"f32": 448.60e6, "f16s": 219.36e6}.get(args.storage) \
+    # fused step on this 128^3 workload (FP32: 262.5 + 186.8 MB; FP16
+    # shifted: 137.7 + 81.8 MB)
+    traffic_fused = {"f32": 449.34e6, "f16s": 219.49e6}.get(args.storage) \
         if w.name == "d3q27_drop_128^3_pr_tr0.7" else None
     if storage != F64:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

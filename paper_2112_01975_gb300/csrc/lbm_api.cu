@@ -233,14 +233,19 @@ dim3 fused_grid(const GeoF &g)
 template <int LAT>
 void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
+    static std::atomic<unsigned long long> done_m{0}, done_f{0};   // devices already opted in
     using L = lbmf::LatF<LAT>;
+    const int bytes = (int)sizeof(lbmf::SharedF<LAT>);
     const dim3 gr = fused_grid<LAT>(h->geof);
-    if (has_solid(h))
-        lbmf::k_step_f32<LAT, true><<<gr, L::TX * L::TY, 0, s>>>(h->geof, h->physf, h->mask, src,
-                                                                dst, h->status);
-    else
-        lbmf::k_step_f32<LAT, false><<<gr, L::TX * L::TY, 0, s>>>(h->geof, h->physf, h->mask, src,
-                                                                 dst, h->status);
+    if (has_solid(h)) {
+        smem_opt_in(lbmf::k_step_f32<LAT, true>, bytes, done_m);
+        lbmf::k_step_f32<LAT, true><<<gr, L::TX * L::TY, bytes, s>>>(h->geof, h->physf, h->mask, src,
+                                                                    dst, h->status);
+    } else {
+        smem_opt_in(lbmf::k_step_f32<LAT, false>, bytes, done_f);
+        lbmf::k_step_f32<LAT, false><<<gr, L::TX * L::TY, bytes, s>>>(h->geof, h->physf, h->mask, src,
+                                                                     dst, h->status);
+    }
 }
 
 template <int LAT, typename ST>
@@ -1009,9 +1014,13 @@ void launch_batch(lbm_batch_ctx *b, int parity, cudaStream_t s)
 {
     if (b->storage == LBM_F16S) launch_batch_shifted<LAT, __half>(b, parity, s);
     else if (b->storage == LBM_BF16S) launch_batch_shifted<LAT, __nv_bfloat16>(b, parity, s);
-    else
-        lbmf::k_step_f32_batch<LAT><<<b->grid, lbmf::LatF<LAT>::TX * lbmf::LatF<LAT>::TY, 0, s>>>(
+    else {
+        static std::atomic<unsigned long long> done{0};   // devices already opted in
+        const int bytes = (int)sizeof(lbmf::SharedF<LAT>);
+        smem_opt_in(lbmf::k_step_f32_batch<LAT>, bytes, done);
+        lbmf::k_step_f32_batch<LAT><<<b->grid, lbmf::LatF<LAT>::TX * lbmf::LatF<LAT>::TY, bytes, s>>>(
             b->d_members[parity], b->d_items, b->n_items);
+    }
 }
 
 void batch_launch(lbm_batch_ctx *b, int parity, cudaStream_t s)

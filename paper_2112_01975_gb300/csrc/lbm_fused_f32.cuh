@@ -7,7 +7,8 @@
 // (rho, s psi) there and rho u_a^3 on the 1-node halo, and keeps them in
 // shared-memory rings. Two planes behind, it collides the tile: the 2-ring
 // force stencils and the Phi differences read only shared memory, the
-// node's own populations are read again (an L2 hit), and the post-collision
+// node's bare velocity and 1/rho come from its phase-A moments through a
+// ring, its populations are read again (an L2 hit), and the post-collision
 // populations are pushed to the neighbours with halfway bounce-back. HBM
 // sees each population read about once and written once; the halo and the
 // second read of a node are served from L2.
@@ -127,7 +128,8 @@ __device__ __forceinline__ int wrapf(int v, int n) { return v < 0 ? v + n : (v >
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Shared-memory rings of one CTA (static size per lattice type).
+// Shared-memory rings of one CTA (size fixed per lattice type; the kernels
+// take it as dynamic shared memory, 63.5 KB for D3Q27).
 template <int LAT> struct SharedF {
     using L = LatF<LAT>;
     static constexpr int TX = L::TX, TY = L::TY, HY = L::HY;
@@ -138,6 +140,7 @@ template <int LAT> struct SharedF {
     float sg[RS][TY][TX];    // sign of P - P0, interior nodes
     float g[GS][3][GY][GX];  // rho u_a^3
     int xw[AX], yw[AY];      // wrapped halo coordinates
+    float4 uv[4][TY][TX];    // (u_x, u_y, u_z, 1/rho) of the interior nodes, from phase A
 };
 
 // Shifted 16-bit storage also keeps the source densities of the planes in
@@ -261,6 +264,7 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                 const int r = k / AX, c = k - r * AX;
                 const bool ring1 = c >= 1 && c < AX - 1 && (!THREE || (r >= 1 && r < AY - 1));
                 float rho, d, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+                float4 uvk = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (solid[u]) {
                     rho = p.rho_w;
                     d = p.spsi_w;
@@ -291,6 +295,7 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                         gx = rho * ux * ux * ux;
                         gy = rho * uy * uy * uy;
                         gz = rho * uz * uz * uz;
+                        uvk = make_float4(ux, uy, uz, inv);
                     }
                     d = excess_pressure_f(p, rho);
                 }
@@ -302,7 +307,10 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                     s_g[gs][2][gr][c - 1] = gz;
                 }
                 const int ir = r - HY, ic = c - 2;
-                if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
+                if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) {
+                    s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
+                    sm.uv[pl & 3][ir][ic] = uvk;
+                }
             }
         }
         __syncthreads();
@@ -389,23 +397,10 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                                : 0.0f;
                 Phi[2] = pref * 0.5f *
                          (s_g[(pc + 1) % GS][2][gr0][gc0] - s_g[(pc - 1) % GS][2][gr0][gc0]);
-                // momentum of the node by x-row sums
-                constexpr int R = Q / 3;
-                float row[R], j[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    row[q] = fi[3 * q] + fi[3 * q + 1] + fi[3 * q + 2];
-                    j[0] += fi[3 * q + 2] - fi[3 * q];
-                }
-#pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const int cy = THREE ? q % 3 - 1 : 0, cz = THREE ? q / 3 - 1 : q - 1;
-                    if (cy > 0) j[1] += row[q];
-                    if (cy < 0) j[1] -= row[q];
-                    if (cz > 0) j[2] += row[q];
-                    if (cz < 0) j[2] -= row[q];
-                }
-                const float inv = __frcp_rn(rho);
+                // bare velocity and 1/rho of the node, formed by phase A from the same populations
+                const float4 uvn = sm.uv[pc & 3][ty][tx];
+                const float inv = uvn.w;
+                const float un[3] = {uvn.x, uvn.y, uvn.z};
                 // product-form factors, paired (equilibrium, extended)
                 float2 ES[3][3];
 #pragma unroll
@@ -414,7 +409,7 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                         ES[1][0] = ES[1][1] = ES[1][2] = f2(1.0f, 1.0f);
                         continue;
                     }
-                    const float ua = j[a] * inv;
+                    const float ua = un[a];
                     const float ze = 1.0f / 3.0f + ua * ua;
                     const float xs = ua + F[a] * inv;
                     const float zs = 1.0f / 3.0f + xs * xs + Phi[a] * inv;
@@ -450,12 +445,14 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
     }
 }
 
+// FP32 populations; dynamic shared memory of sizeof(SharedF<LAT>).
 template <int LAT, bool MASK>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
 k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
            float *__restrict__ fout, int *__restrict__ status)
 {
-    __shared__ SharedF<LAT> sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedF<LAT> &sm = *reinterpret_cast<SharedF<LAT> *>(smem_raw);
     fused_tile<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
@@ -493,13 +490,15 @@ struct WorkItem {
 };
 
 // Persistent: CTA b takes items b, b + gridDim.x, ... (a fixed assignment,
-// so each member's result does not depend on what else is in the batch).
+// so each member's result does not depend on what else is in the batch);
+// dynamic shared memory of sizeof(SharedF<LAT>).
 template <int LAT>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
 k_step_f32_batch(const MemberF *__restrict__ members, const WorkItem *__restrict__ items,
                  int n_items)
 {
-    __shared__ SharedF<LAT> sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedF<LAT> &sm = *reinterpret_cast<SharedF<LAT> *>(smem_raw);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         const MemberF &m = members[w.member];
