@@ -129,7 +129,7 @@ __device__ __forceinline__ int wrapf(int v, int n) { return v < 0 ? v + n : (v >
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Shared-memory rings of one CTA (size fixed per lattice type; the kernels
-// take it as dynamic shared memory, 63.5 KB for D3Q27).
+// take it as dynamic shared memory, 63,856 bytes for D3Q27).
 template <int LAT> struct SharedF {
     using L = LatF<LAT>;
     static constexpr int TX = L::TX, TY = L::TY, HY = L::HY;
