@@ -53,7 +53,7 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (an FMA-chain probe measured
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d3q27_drop_128^3_pr_tr0.7")
@@ -81,7 +81,9 @@ def dist_setup(n_gpus):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons: one `nvidia-smi -lms 100`
+    process, started (and seen to answer) before the timed region; the rows
+    that arrive while the region runs are kept."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -89,42 +91,57 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.index = index
-        self.rows = []
-        self._stop = threading.Event()
+        self.rows = []          # (arrival time, fields)
+        self.proc = None
         self._t = None
+        self.t0 = self.t1 = 0.0
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([c.strip() for c in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self.proc.stdout:
+            line = line.strip()
+            if line:
+                self.rows.append((time.monotonic(), [c.strip() for c in line.split(",")]))
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            deadline = time.monotonic() + 5.0
+            while not self.rows and time.monotonic() < deadline and self.proc.poll() is None:
+                time.sleep(0.02)
+        except Exception:
+            self.proc = None
+        self.t0 = time.monotonic()
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        self.t1 = time.monotonic()
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self._t.join(timeout=5)
 
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        rows = [r for t, r in self.rows if self.t0 <= t <= self.t1]
+        if not rows:   # a region shorter than the 100 ms period: the last row before its end
+            rows = [r for t, r in self.rows if t <= self.t1][-1:] or [self.rows[0][1]]
+        sm = [float(r[1]) for r in rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows for k in range(4)
+        reasons = sorted({names[k] for r in rows for k in range(4)
                           if len(r) > 5 + k and r[5 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+                "samples": len(rows)}
 
 
 def measured_peaks():
