@@ -169,14 +169,12 @@ def host_cpu() -> dict:
 
 
 def oracle_sample_mlups(w, target_s: float = 12.0, openmp: bool = False):
-    """FP64 oracle throughput on a centred crop of the workload: one host
-    thread, or (openmp) the -fopenmp build of the same source on all cores."""
+    """FP64 oracle throughput on the workload scaled to 48^3 (64^2 in 2D): one
+    host thread, or (openmp) the -fopenmp build of the same source on all cores."""
     from oracle.lbm import OracleLBM
-    from paper_2112_01975_gb300 import inputs
     n = 48 if w.lattice == 1 else 64
     nz = n if w.lattice == 1 else 1
-    rho = inputs.add_noise(inputs.drop(n, n, nz, w.radius * n / w.nx, w.rho_v, w.rho_l),
-                           w.noise, w.seed)
+    rho = w.rho0_scaled(n)
     o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
                   openmp=openmp)
     o.init(rho)
@@ -186,20 +184,19 @@ def oracle_sample_mlups(w, target_s: float = 12.0, openmp: bool = False):
         o.step(1)
         steps += 1
     dt = time.perf_counter() - t0
-    return n * n * nz * steps / dt / 1e6, f"{n}x{n}x{nz} centred crop of the workload, {steps} steps, {dt:.1f} s"
+    return n * n * nz * steps / dt / 1e6, (f"the workload scaled to {n}x{n}x{nz} (radius and drop "
+                                           f"centres x {n}/{w.nx}), {steps} steps, {dt:.1f} s")
 
 
 def run_reference(args, w, world, rank):
     """The CPU oracle as it stands, one host thread, each step one lattice
-    update of a 32^3 (3D) or 64^2 (2D) crop of the workload."""
+    update of the workload scaled to 32^3 (3D) or 64^2 (2D)."""
     if rank != 0:
         return
     from oracle.lbm import OracleLBM
-    from paper_2112_01975_gb300 import inputs
     n = 32 if w.lattice == 1 else 64
     nz = n if w.lattice == 1 else 1
-    rho = inputs.add_noise(inputs.drop(n, n, nz, w.radius * n / w.nx, w.rho_v, w.rho_l),
-                           w.noise, w.seed)
+    rho = w.rho0_scaled(n)
     o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b)
     o.init(rho)
     for _ in range(args.warmup):
@@ -209,7 +206,8 @@ def run_reference(args, w, world, rank):
         o.step(1)
     dt = time.perf_counter() - t0
     mlups = n * n * nz * args.steps / dt / 1e6
-    sample = f"{n}x{n}x{nz} centred crop of {w.name}, one lattice update per step"
+    sample = (f"{w.name} scaled to {n}x{n}x{nz} (radius and drop centres x {n}/{w.nx}), "
+              "one lattice update per step")
     print(json.dumps({
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

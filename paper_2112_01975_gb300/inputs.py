@@ -137,13 +137,30 @@ class Workload:
     b: float
     noise: float = 1e-4
     steps: int = 1000
+    centres: tuple = ()   # several drops of the same radius; empty: one drop at the centre
 
     @property
     def nodes(self) -> int:
         return self.nx * self.ny * self.nz
 
     def rho0(self) -> np.ndarray:
-        r = drop(self.nx, self.ny, self.nz, self.radius, self.rho_v, self.rho_l)
+        if self.centres:
+            r = drops(self.nx, self.ny, self.nz, list(self.centres), self.radius, self.rho_v,
+                      self.rho_l)
+        else:
+            r = drop(self.nx, self.ny, self.nz, self.radius, self.rho_v, self.rho_l)
+        return add_noise(r, self.noise, self.seed)
+
+    def rho0_scaled(self, n: int) -> np.ndarray:
+        """The same layout on an n^3 (3D) or n^2 (2D) lattice: radius and
+        drop centres scaled by n / nx; the same noise amplitude and seed."""
+        s = n / self.nx
+        nz = n if self.lattice == 1 else 1
+        if self.centres:
+            r = drops(n, n, nz, [tuple(c * s for c in cc) for cc in self.centres], self.radius * s,
+                      self.rho_v, self.rho_l)
+        else:
+            r = drop(n, n, nz, self.radius * s, self.rho_v, self.rho_l)
         return add_noise(r, self.noise, self.seed)
 
     def u0(self) -> np.ndarray:
@@ -176,4 +193,14 @@ DROP_D3Q27_128 = Workload("d3q27_drop_128^3_pr_tr0.7", 1, 128, 128, 128, 1, 0.7,
 DROP_D3Q27_96 = dataclasses.replace(DROP_D3Q27_128, name="d3q27_drop_96^3_pr_tr0.7", nx=96,
                                     ny=96, nz=96, radius=18.0)
 
-WORKLOADS = {w.name: w for w in (DROP_D2Q9_64, DROP_D3Q27_128, DROP_D3Q27_96)}
+# D3Q27 coalescence, 256^3 periodic, Peng-Robinson (b = 2/21, a scaled for a
+# liquid dP/drho of 0.1) at T/Tc = 0.45 (Maxwell density ratio 6.6e4): two
+# drops of radius 40 touching at the centre, tau = 0.725.
+COALESCENCE_D3Q27_256 = Workload("d3q27_coalescence_256^3_pr_tr0.45", 1, 256, 256, 256, 1, 0.45,
+                                 kappa=0.0100296894491, tau=0.725,
+                                 rho_v=0.000142187914218311, rho_l=9.42493892983339,
+                                 radius=40.0, seed=3, a=0.00162040657246882, b=2.0 / 21.0,
+                                 steps=10000, centres=((88.0, 128.0, 128.0), (168.0, 128.0, 128.0)))
+
+WORKLOADS = {w.name: w for w in (DROP_D2Q9_64, DROP_D3Q27_128, DROP_D3Q27_96,
+                                 COALESCENCE_D3Q27_256)}

@@ -133,7 +133,8 @@ def test_width_scales_as_sqrt_kappa_over_a():
     assert ph.interface_width(e2, 0.1) == pytest.approx(math.sqrt(10) * w1, rel=1e-9)
 
 
-@pytest.mark.parametrize("w", [inputs.DROP_D2Q9_64, inputs.DROP_D3Q27_128])
+@pytest.mark.parametrize("w", [inputs.DROP_D2Q9_64, inputs.DROP_D3Q27_128,
+                               inputs.COALESCENCE_D3Q27_256])
 def test_workload_constants_match_maxwell(w):
     """The stored init densities and kappa of each workload come from the EOS."""
     e = EOS(w.eos, w.t_over_tc, a=w.a, b=w.b)
