@@ -486,7 +486,8 @@ def main():
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
     # fused step on this 128^3 workload (FP32: 262.5 + 186.8 MB; FP16
     # shifted: 137.7 + 81.8 MB)
-    traffic_fused = {"f32": 449.34e6, "f16s": 219.49e6}.get(args.storage) \
+    tile = g.tile()
+    traffic_fused = {("f32", 8): 449.34e6, ("f16s", 8): 219.49e6}.get((args.storage, tile[1])) \
         if w.name == "d3q27_drop_128^3_pr_tr0.7" else None
     if storage != F64:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -495,7 +496,7 @@ def main():
                     "kernel": "k_step_f32 (fused step)" if storage == F32 else "k_step_shifted",
                     "peak_source": peak_kind + " hbm_gbs",
                     "alg_bytes_per_launch": alg, "ms_per_launch": ms_collide,
-                    "chunk": chunk}
+                    "chunk": chunk, "tile": f"{tile[0]}x{tile[1]}"}
     else:
         tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,

@@ -235,9 +235,26 @@ int lbm_set_chunk(lbm_handle h, int chunk);
 /* Pick the chunk of the fused FP32 step by timing candidates on the
  * handle's own state (saved to a temporary device buffer and restored
  * afterwards, so the state is unchanged). Sets and returns it in
- * *chunk_out (0 for FP64 storage, which has no tile parameter).
- * Synchronising; allocates and frees one state-sized buffer. */
+ * *chunk_out (0 for FP64 storage, which has no tile parameter). For D3Q27
+ * with LBM_F32 storage it also picks the tile height, 8 or 7 rows of 32
+ * nodes (7 rows fill every SM with two CTAs in one wave where 8 rows leave
+ * some SMs with one, e.g. at 128^3); the shifted storages and batches keep
+ * 8 rows. Tiles and chunks change the work split only: results are
+ * bitwise the same. Synchronising; allocates and frees one state-sized
+ * buffer. */
 int lbm_autotune(lbm_handle h, int *chunk_out);
+
+/* The tile of the fused step in use, in nodes: *tile_x = 32, *tile_y = 8 or
+ * 7 (D3Q27; 7 only after lbm_autotune chose it), or 128 x 1 for D2Q9 rows;
+ * 0 x 0 for LBM_F64 storage, which runs one thread per node. Either pointer
+ * may be NULL. */
+int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y);
+
+/* Set the tile height of the D3Q27 LBM_F32 fused step: 8 (the default) or 7
+ * rows of 32 nodes. Results are bitwise the same; only the work split and
+ * the speed change. LBM_EINVAL for another height, another lattice or
+ * storage. */
+int lbm_set_tile(lbm_handle h, int tile_y);
 
 /* ---- Batches: many lattices advanced by one persistent launch ----------
  * A batch holds count >= 1 distinct, initialised handles with the same

@@ -14,6 +14,7 @@
 
 #include "lbm.h"
 #include "lbm_fused_f32.cuh"
+#include "lbm_fused_f32_r7.cuh"
 #include "lbm_kernels.cuh"
 
 using lbmk::Geo;
@@ -27,6 +28,7 @@ struct lbm_ctx {
     Phys phys;
     GeoF geof;     // FP32 fused step: 3D frame (D2Q9: ny = 1, nz = 2D y extent)
     PhysF physf;
+    int tile_rows = 8;   // D3Q27 FP32 step: 32 x 8 (lbmf) or 32 x 7 (lbmf7) tiles
     int storage, flags;
     double t_over_tc, tau;
     std::vector<uint8_t> mask_host;
@@ -223,16 +225,43 @@ double *f64(lbm_ctx *h, int k) { return static_cast<double *>(h->fv[k]); }
 float *f32(lbm_ctx *h, int k) { return static_cast<float *>(h->fv[k]); }
 
 template <int LAT>
-dim3 fused_grid(const GeoF &g)
+dim3 fused_grid(const GeoF &g, int rows = lbmf::LatF<LAT>::TY)
 {
     using L = lbmf::LatF<LAT>;
-    return dim3((g.nx + L::TX - 1) / L::TX, (g.ny + L::TY - 1) / L::TY,
-                (g.nz + g.chunk - 1) / g.chunk);
+    const int ty = LAT == 1 ? rows : L::TY;
+    return dim3((g.nx + L::TX - 1) / L::TX, (g.ny + ty - 1) / ty, (g.nz + g.chunk - 1) / g.chunk);
+}
+
+// The same parameters as the 7-row build's types (one source, one layout).
+template <typename T, typename U>
+T as_layout(const U &u)
+{
+    static_assert(sizeof(T) == sizeof(U), "same source, same layout");
+    T t;
+    memcpy(&t, &u, sizeof t);
+    return t;
+}
+
+template <bool MASK>
+void launch_fused_r7(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    using L = lbmf7::LatF<1>;
+    const int bytes = (int)sizeof(lbmf7::SharedF<1>);
+    smem_opt_in(lbmf7::k_step_f32<1, MASK>, bytes, done);
+    lbmf7::k_step_f32<1, MASK><<<fused_grid<1>(h->geof, L::TY), L::TX * L::TY, bytes, s>>>(
+        as_layout<lbmf7::GeoF>(h->geof), as_layout<lbmf7::PhysF>(h->physf), h->mask, src, dst,
+        h->status);
 }
 
 template <int LAT>
 void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
+    if (LAT == 1 && h->tile_rows == 7) {
+        if (has_solid(h)) launch_fused_r7<true>(h, s, src, dst);
+        else              launch_fused_r7<false>(h, s, src, dst);
+        return;
+    }
     static std::atomic<unsigned long long> done_m{0}, done_f{0};   // devices already opted in
     using L = lbmf::LatF<LAT>;
     const int bytes = (int)sizeof(lbmf::SharedF<LAT>);
@@ -1275,17 +1304,25 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
                               cudaMemcpyDeviceToDevice, h->stream));
     const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128};
     const int nz = h->geof.nz;
-    int best = h->geof.chunk;
+    // D3Q27 FP32: 32 x 8 and 32 x 7 tiles (the shifted and batched steps use 32 x 8)
+    const bool two_heights = h->lattice == LBM_D3Q27 && h->storage == LBM_F32;
+    int best = h->geof.chunk, best_rows = h->tile_rows;
     double best_ms = 1e30;
-    for (int c : cands) {
-        if (c > nz && c != cands[0]) continue;
-        h->geof.chunk = c;
-        double ms[2];
-        rc = lbm_time_kernels(h, 1, ms);                  // warm-up
-        if (rc == LBM_OK) rc = lbm_time_kernels(h, 6, ms);
+    for (int rows : {8, 7}) {
+        if (rows == 7 && !two_heights) continue;
+        h->tile_rows = rows;
+        for (int c : cands) {
+            if (c > nz && c != cands[0]) continue;
+            h->geof.chunk = c;
+            double ms[2];
+            rc = lbm_time_kernels(h, 1, ms);                  // warm-up
+            if (rc == LBM_OK) rc = lbm_time_kernels(h, 6, ms);
+            if (rc != LBM_OK) break;
+            if (ms[1] < best_ms) { best_ms = ms[1]; best = c; best_rows = rows; }
+        }
         if (rc != LBM_OK) break;
-        if (ms[1] < best_ms) { best_ms = ms[1]; best = c; }
     }
+    h->tile_rows = best_rows;
     cudaError_t e = cudaMemcpyAsync(h->fv[0], save, bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess && rbytes)
         e = cudaMemcpyAsync(h->rs[0], static_cast<char *>(save) + bytes, rbytes,
@@ -1305,6 +1342,34 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
         h->graph = nullptr;
     }
     if (chunk_out) *chunk_out = best;
+    return LBM_OK;
+}
+
+int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y)
+{
+    if (!h) return LBM_EINVAL;
+    int tx = 0, ty = 0;
+    if (h->storage != LBM_F64) {
+        tx = h->lattice == LBM_D2Q9 ? lbmf::LatF<0>::TX : lbmf::LatF<1>::TX;
+        ty = h->lattice == LBM_D2Q9 ? lbmf::LatF<0>::TY
+             : (h->tile_rows == 7 && h->storage == LBM_F32) ? 7 : lbmf::LatF<1>::TY;
+    }
+    if (tile_x) *tile_x = tx;
+    if (tile_y) *tile_y = ty;
+    return LBM_OK;
+}
+
+int lbm_set_tile(lbm_handle h, int tile_y)
+{
+    if (!h) return LBM_EINVAL;
+    if (h->lattice != LBM_D3Q27 || h->storage != LBM_F32)
+        return fail(h, LBM_EINVAL, "the tile height is a parameter of the D3Q27 FP32 step only");
+    if (tile_y != 7 && tile_y != 8) return fail(h, LBM_EINVAL, "tile height must be 7 or 8");
+    if (h->tile_rows != tile_y && h->graph) {   // the captured graph holds the other kernel
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->tile_rows = tile_y;
     return LBM_OK;
 }
 

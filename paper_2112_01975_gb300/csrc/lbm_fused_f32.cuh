@@ -1,534 +1,10 @@
-// Fused single-pass step for FP32 populations with FP32 arithmetic.
-//
-// One CTA owns a TX x TY column tile of the x-y plane and marches along z
-// through a chunk of planes (D2Q9 runs as a 3D lattice with one y row and
-// the 2D y axis as the march axis). For each plane that enters, it reads the
-// 27 populations of every node of the tile plus a 2-node halo, forms
-// (rho, s psi) there and rho u_a^3 on the 1-node halo, and keeps them in
-// shared-memory rings. Two planes behind, it collides the tile: the 2-ring
-// force stencils and the Phi differences read only shared memory, the
-// node's bare velocity and 1/rho come from its phase-A moments through a
-// ring, its populations are read again (an L2 hit), and the post-collision
-// populations are pushed to the neighbours with halfway bounce-back. HBM
-// sees each population read about once and written once; the halo and the
-// second read of a node are served from L2.
+// Fused single-pass step, D3Q27 tiles of 32 x 8 nodes (namespace lbmf; the
+// D2Q9 tile is a 128-wide row in every build). The code is in
+// lbm_fused_f32_body.cuh.
 #pragma once
 
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-namespace lbmf {
-
-// Storage of populations: float (FP32), or 16-bit values of the relative
-// shift h_i = f_i / rho(src) - w_i, with rho(src) the FP32 density of the node
-// that pushed the population (the node itself after a bounce-back). Relative
-// to the source density, h stays O(1e-3) in a vapour of any density, where
-// the absolute shift f_i - w_i rho would fall below FP16's normal range.
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <typename ST> __device__ __forceinline__ ST from_f(float v);
-template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v)
-{
-    return __float2bfloat16_rn(v);
-}
-template <typename ST> struct IsShifted { static constexpr bool value = true; };
-template <> struct IsShifted<float> { static constexpr bool value = false; };
-
-struct GeoF {
-    int nx, ny, nz;   // as stored; D2Q9: ny = 1 and nz = the 2D y extent
-    unsigned N;
-    int chunk;        // planes per CTA along z
-};
-
-struct PhysF {
-    int eos;
-    float a, b, RT, aalpha;
-    float kappa, omega, omw, phi_pref;  // omw = 1 - omega
-    float rho_w, spsi_w;                // virtual solid density and its P - P0
-    float g[3];                         // body acceleration in the kernel frame (D2Q9: gx, 0, gy)
-    int var_visc;                       // density-dependent relaxation (nu linear in rho)
-    float nu_l, nu_v, visc_rl, inv_drho, phi_sign;   // inv_drho = 1 / (rho_l - rho_v)
-};
-
-// Relaxation rate at density rho: nu from nu_l at rho_l to nu_v at rho_v,
-// linear in rho and constant beyond (used only when var_visc).
-__device__ __forceinline__ float omega_var_f(const PhysF &p, float rho)
-{
-    const float t = fminf(fmaxf((p.visc_rl - rho) * p.inv_drho, 0.0f), 1.0f);
-    return __frcp_rn(3.0f * fmaf(p.nu_v - p.nu_l, t, p.nu_l) + 0.5f);
-}
-
-// Lattice description in the 3D frame: D2Q9 uses (cx, 0, cy).
-template <int LAT> struct LatF;
-template <> struct LatF<0> {
-    static constexpr int Q = 9, TX = 128, TY = 1, HY = 0;
-    __device__ static constexpr int cx(int i) { return i % 3 - 1; }
-    __device__ static constexpr int cy(int) { return 0; }
-    __device__ static constexpr int cz(int i) { return i / 3 - 1; }
-};
-template <> struct LatF<1> {
-    static constexpr int Q = 27, TX = 32, TY = 8, HY = 2;
-    __device__ static constexpr int cx(int i) { return i % 3 - 1; }
-    __device__ static constexpr int cy(int i) { return (i / 3) % 3 - 1; }
-    __device__ static constexpr int cz(int i) { return i / 9 - 1; }
-};
-
-// Lattice weight w_i = prod of 1D weights 2/3 (c = 0), 1/6 (c = +-1) (Eq. wi).
-template <int LAT> __device__ __forceinline__ constexpr float weight_f(int i)
-{
-    using L = LatF<LAT>;
-    return (L::cx(i) ? 1.0f / 6.0f : 2.0f / 3.0f) * (LAT == 1 ? (L::cy(i) ? 1.0f / 6.0f : 2.0f / 3.0f) : 1.0f) *
-           (L::cz(i) ? 1.0f / 6.0f : 2.0f / 3.0f);
-}
-
-// P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 and Appendix C equations of state).
-// Every operation is an explicitly rounded intrinsic, so each inlined call
-// site rounds the same way (no call-site-dependent contraction).
-__device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
-{
-    const float br = __fmul_rn(p.b, rho), rr = __fmul_rn(rho, rho);
-    const float nr3 = __fmul_rn(rho, -1.0f / 3.0f);
-    const float rt = __fmul_rn(rho, p.RT);
-    switch (p.eos) {
-    case 0:   // rho RT / (1 - b rho) - a rho^2 - rho/3
-        return __fmaf_rn(-p.a, rr, __fmaf_rn(rt, __frcp_rn(__fsub_rn(1.0f, br)), nr3));
-    case 1: {   // PR: d1 = 1 - b rho, d2 = 1 + 2 b rho - (b rho)^2
-        const float d1 = __fsub_rn(1.0f, br), d2 = __fmaf_rn(br, __fsub_rn(2.0f, br), 1.0f);
-        const float num = __fmaf_rn(rt, d2, -__fmul_rn(__fmul_rn(p.aalpha, rr), d1));
-        return __fmaf_rn(num, __frcp_rn(__fmul_rn(d1, d2)), nr3);
-    }
-    case 2: {   // RKS: d1 = 1 - b rho, d2 = 1 + b rho
-        const float d1 = __fsub_rn(1.0f, br), d2 = __fadd_rn(1.0f, br);
-        const float num = __fmaf_rn(rt, d2, -__fmul_rn(__fmul_rn(p.aalpha, rr), d1));
-        return __fmaf_rn(num, __frcp_rn(__fmul_rn(d1, d2)), nr3);
-    }
-    case 4: {   // Shan-Chen, psi_SC = 1 - exp(-rho): P - rho/3 = (G/6) psi_SC^2, G in RT
-        const float q = __fsub_rn(1.0f, expf(-rho));
-        return __fmul_rn(__fmul_rn(q, q), __fmul_rn(p.RT, 1.0f / 6.0f));
-    }
-    case 5: {   // Shan-Chen, psi_SC = exp(-1/rho)
-        const float q = expf(-__frcp_rn(rho));
-        return __fmul_rn(__fmul_rn(q, q), __fmul_rn(p.RT, 1.0f / 6.0f));
-    }
-    default: {   // CS with e = b rho / 4
-        const float e = __fmul_rn(0.25f, br), om = __fsub_rn(1.0f, e);
-        const float poly = __fmaf_rn(__fmul_rn(e, e), __fsub_rn(1.0f, e), __fadd_rn(1.0f, e));
-        const float den = __fmul_rn(__fmul_rn(om, om), om);
-        return __fmaf_rn(-p.a, rr, __fmaf_rn(__fmul_rn(rt, poly), __frcp_rn(den), nr3));
-    }
-    }
-}
-
-__device__ __forceinline__ int wrapf(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-// Shared-memory rings of one CTA (size fixed per lattice type; the kernels
-// take it as dynamic shared memory, 63,856 bytes for D3Q27).
-template <int LAT> struct SharedF {
-    using L = LatF<LAT>;
-    static constexpr int TX = L::TX, TY = L::TY, HY = L::HY;
-    static constexpr int AX = TX + 4, AY = TY + 2 * HY;               // (rho, |psi|) halo tile
-    static constexpr int GX = TX + 2, GY = LAT == 1 ? TY + 2 : 1;     // rho u^3 halo tile
-    static constexpr int RS = 6, GS = 5;                               // ring slots
-    float2 rp[RS][AY][AX];   // (rho, |psi|)
-    float sg[RS][TY][TX];    // sign of P - P0, interior nodes
-    float g[GS][3][GY][GX];  // rho u_a^3
-    int xw[AX], yw[AY];      // wrapped halo coordinates
-    float4 uv[4][TY][TX];    // (u_x, u_y, u_z, 1/rho) of the interior nodes, from phase A
-};
-
-// Shifted 16-bit storage also keeps the source densities of the planes in
-// flight on a 3-node halo (the sources of the 2-halo's populations).
-template <int LAT> struct SharedS : SharedF<LAT> {
-    static constexpr int RX = SharedF<LAT>::AX + 2, RY = LAT == 1 ? SharedF<LAT>::AY + 2 : 1;
-    static constexpr int QS = 8;   // ring slots (planes pl-4 .. pl+2 live)
-    float rs[QS][RY][RX];
-    int rxw[RX], ryw[RY];
-};
-
-// Population i of the node at halo coordinates (r, c) of ring plane q:
-// stored value plus w_i times the density of its source node.
-template <int LAT, typename ST, typename SM>
-__device__ __forceinline__ float decode_pop(ST hv, int i, int r, int c, int q, const SM &sm)
-{
-    if constexpr (IsShifted<ST>::value) {
-        using L = LatF<LAT>;
-        const int rr = r + (LAT == 1 ? 1 : 0) - L::cy(i), cc = c + 1 - L::cx(i);
-        return (weight_f<LAT>(i) + to_f(hv)) * sm.rs[(q - L::cz(i) + SM::QS) & (SM::QS - 1)][rr][cc];
-    } else {
-        return to_f(hv);
-    }
-}
-
-// Source densities of one plane (ring index q) on the 3-halo into the ring.
-template <int LAT, typename SM>
-__device__ __forceinline__ void load_rho_plane(SM &sm, const GeoF &g, const float *__restrict__ rho_src,
-                                               int z0, int q)
-{
-    constexpr int RX = SM::RX, RY = SM::RY, QS = SM::QS;
-    constexpr int NT = LatF<LAT>::TX * LatF<LAT>::TY;
-    const int zq = ((z0 - 2 + q) % g.nz + g.nz) % g.nz;
-    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
-    for (int k = threadIdx.x; k < RX * RY; k += NT) {
-        const int r = k / RX, c = k - r * RX;
-        sm.rs[(q + QS) & (QS - 1)][r][c] =
-            __ldg(rho_src + ((unsigned)sm.rxw[c] + (unsigned)g.nx * (unsigned)sm.ryw[r] + plane * (unsigned)zq));
-    }
-}
-
-// One CTA's work: the column tile (bx, by) over the plane chunk bz.
-template <int LAT, bool MASK, typename ST = float, typename SM = SharedF<LAT>>
-__device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
-                                           const uint8_t *__restrict__ mask,
-                                           const ST *__restrict__ f, ST *__restrict__ fout,
-                                           int *__restrict__ status, int bx, int by, int bz,
-                                           SM &sm, const float *__restrict__ rho_src = nullptr,
-                                           float *__restrict__ rho_dst = nullptr)
-{
-    constexpr bool SHIFT = IsShifted<ST>::value;
-    static_assert(!(SHIFT && MASK), "shifted storage runs lattices without solid nodes");
-    using L = LatF<LAT>;
-    constexpr int Q = L::Q, TX = L::TX, TY = L::TY, HY = L::HY;
-    constexpr bool THREE = LAT == 1;
-    constexpr int NT = TX * TY;
-    constexpr int AX = SharedF<LAT>::AX, AY = SharedF<LAT>::AY;
-    constexpr int RS = SharedF<LAT>::RS, GS = SharedF<LAT>::GS;
-    auto &s_rp = sm.rp;
-    auto &s_sg = sm.sg;
-    auto &s_g = sm.g;
-    auto &s_xw = sm.xw;
-    auto &s_yw = sm.yw;
-
-    const int tid = threadIdx.x;
-    const int x0 = bx * TX, y0 = by * TY;
-    const int z0 = bz * g.chunk;
-    const int z1 = min(z0 + g.chunk, g.nz);
-    const int tx = tid % TX, ty = tid / TX;
-    const int xi = x0 + tx, yi = y0 + ty;
-    const bool inside = xi < g.nx && yi < g.ny;
-    const unsigned N = g.N;
-    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
-    for (int c = tid; c < AX; c += NT) s_xw[c] = ((x0 - 2 + c) % g.nx + g.nx) % g.nx;
-    for (int r = tid; r < AY; r += NT) s_yw[r] = THREE ? ((y0 - HY + r) % g.ny + g.ny) % g.ny : 0;
-    if constexpr (SHIFT) {
-        for (int c = tid; c < SM::RX; c += NT) sm.rxw[c] = ((x0 - 3 + c) % g.nx + g.nx) % g.nx;
-        for (int r = tid; r < SM::RY; r += NT)
-            sm.ryw[r] = THREE ? ((y0 - HY - 1 + r) % g.ny + g.ny) % g.ny : 0;
-        __syncthreads();
-        load_rho_plane<LAT>(sm, g, rho_src, z0, -1);
-        load_rho_plane<LAT>(sm, g, rho_src, z0, 0);
-        load_rho_plane<LAT>(sm, g, rho_src, z0, 1);
-    }
-    __syncthreads();
-
-    // Planes z0-2 .. z1+1 enter the rings one per iteration; plane z0-2+pl
-    // has ring index pl. Six (rho, |psi|) slots and five rho u^3 slots let
-    // the next plane enter while slower warps still collide: one barrier
-    // per plane.
-    const int np = (z1 - z0) + 4;
-    for (int pl = 0; pl < np; ++pl) {
-        // ---- phase A: plane z0 - 2 + pl enters the rings -------------------
-        // Each thread owns up to KA halo nodes and issues all their loads
-        // before any arithmetic, for memory-level parallelism.
-        {
-            constexpr int KA = (AX * AY + NT - 1) / NT;
-            const int zl = wrapf(z0 - 2 + pl, g.nz);
-            const int rs = pl % RS, gs = pl % GS;
-            float fi[KA][Q];
-            unsigned nk[KA];
-            bool live[KA], solid[KA];
-            if constexpr (SHIFT) load_rho_plane<LAT>(sm, g, rho_src, z0, pl + 2);   // for the next iteration
-#pragma unroll
-            for (int u = 0; u < KA; ++u) {
-                const int k = tid + u * NT;
-                live[u] = k < AX * AY;
-                const int kk = live[u] ? k : 0;
-                const int r = kk / AX, c = kk - r * AX;
-                nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
-                solid[u] = MASK && live[u] && mask[nk[u]];
-                if (live[u] && !solid[u]) {
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < KA; ++u) {
-                if (!live[u]) continue;
-                const int k = tid + u * NT;
-                const int r = k / AX, c = k - r * AX;
-                const bool ring1 = c >= 1 && c < AX - 1 && (!THREE || (r >= 1 && r < AY - 1));
-                float rho, d, gx = 0.0f, gy = 0.0f, gz = 0.0f;
-                float4 uvk = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (solid[u]) {
-                    rho = p.rho_w;
-                    d = p.spsi_w;
-                } else {
-                    // x-row sums for each (cy, cz), then the moments from them
-                    constexpr int R = Q / 3;
-                    float row[R], jx = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        row[q] = fi[u][3 * q] + fi[u][3 * q + 1] + fi[u][3 * q + 2];
-                        jx += fi[u][3 * q + 2] - fi[u][3 * q];
-                    }
-                    rho = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < R; ++q) rho += row[q];
-                    if (ring1) {
-                        float jy = 0.0f, jz = 0.0f;
-#pragma unroll
-                        for (int q = 0; q < R; ++q) {
-                            const int cy = THREE ? q % 3 - 1 : 0, cz = THREE ? q / 3 - 1 : q - 1;
-                            if (cy > 0) jy += row[q];
-                            if (cy < 0) jy -= row[q];
-                            if (cz > 0) jz += row[q];
-                            if (cz < 0) jz -= row[q];
-                        }
-                        const float inv = __frcp_rn(rho);
-                        const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-                        gx = rho * ux * ux * ux;
-                        gy = rho * uy * uy * uy;
-                        gz = rho * uz * uz * uz;
-                        uvk = make_float4(ux, uy, uz, inv);
-                    }
-                    d = excess_pressure_f(p, rho);
-                }
-                s_rp[rs][r][c] = f2(rho, sqrtf(fabsf(d)));
-                if (ring1) {
-                    const int gr = THREE ? r - 1 : 0;
-                    s_g[gs][0][gr][c - 1] = gx;
-                    s_g[gs][1][gr][c - 1] = gy;
-                    s_g[gs][2][gr][c - 1] = gz;
-                }
-                const int ir = r - HY, ic = c - 2;
-                if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) {
-                    s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
-                    sm.uv[pl & 3][ir][ic] = uvk;
-                }
-            }
-        }
-        __syncthreads();
-        // ---- phase B: collide plane zc = z0 + pl - 4 --------------------------
-        if (pl >= 4 && inside) {
-            const int pc = pl - 2;             // ring index of the collided plane
-            const int zc = z0 + pl - 4;
-            const unsigned n = (unsigned)xi + (unsigned)g.nx * (unsigned)yi + plane * (unsigned)zc;
-            if (!(MASK && mask[n])) {
-                // the node's own populations (second read, an L2 hit), issued first
-                float fi[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
-                const int cr = ty + HY, cc = tx + 2;
-                const float2 c0 = s_rp[pc % RS][cr][cc];
-                const float rho = c0.x;
-                const float spsi = s_sg[pc % RS][ty][tx] * c0.y;
-                if (!(rho > 0.0f) || !isfinite(rho)) atomicOr(status, 1);
-                if constexpr (SHIFT) rho_dst[n] = rho;   // source density of what this node pushes
-                // Korteweg force (Eq. Kforce_final, sign as the force on the fluid).
-                // Per ring s, the pairs (|psi|, rho) of neighbours with c_a = +1 and
-                // c_a = -1 are summed by weight class (centre, edge, corner).
-                int slot[5];
-#pragma unroll
-                for (int dz = 0; dz < 5; ++dz) slot[dz] = (pc - 2 + dz) % RS;
-                float2 S[3] = {f2(0.0f, 0.0f), f2(0.0f, 0.0f), f2(0.0f, 0.0f)};   // (S_psi, S_rho)
-                const float2 neg1 = f2(-1.0f, -1.0f);
-#pragma unroll
-                for (int s = 1; s <= 2; ++s) {
-                    float2 P[3][3], M[3][3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) { P[a][k] = f2(0.0f, 0.0f); M[a][k] = f2(0.0f, 0.0f); }
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
-                        if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
-                        const float2 r2 = s_rp[slot[2 + s * c[2]]][cr + s * c[1]][cc + s * c[0]];
-                        const float2 v = f2(r2.y, r2.x);   // (|psi|, rho)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            if (c[a] == 0) continue;
-                            const int k = (a != 0 && c[0] != 0) + (a != 1 && c[1] != 0) +
-                                          (a != 2 && c[2] != 0);
-                            if (c[a] > 0) P[a][k] = __fadd2_rn(P[a][k], v);
-                            else          M[a][k] = __fadd2_rn(M[a][k], v);
-                        }
-                    }
-                    // weights w_i/cs2 c_a = 1/2 W(c_b) W(c_c): D3Q27 2/9, 1/18, 1/72;
-                    // D2Q9 1/3, 1/12; ring coefficients (4/3, 2) and (-1/6, -1)
-                    const float2 gsr = s == 1 ? f2(4.0f / 3.0f, 2.0f) : f2(-1.0f / 6.0f, -1.0f);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        if (!THREE && a == 1) continue;
-                        const float2 D0 = __ffma2_rn(M[a][0], neg1, P[a][0]);
-                        const float2 D1 = __ffma2_rn(M[a][1], neg1, P[a][1]);
-                        float2 Dw;
-                        if (THREE) {
-                            const float2 D2 = __ffma2_rn(M[a][2], neg1, P[a][2]);
-                            Dw = __fmul2_rn(D0, f2(2.0f / 9.0f, 2.0f / 9.0f));
-                            Dw = __ffma2_rn(D1, f2(1.0f / 18.0f, 1.0f / 18.0f), Dw);
-                            Dw = __ffma2_rn(D2, f2(1.0f / 72.0f, 1.0f / 72.0f), Dw);
-                        } else {
-                            Dw = __fmul2_rn(D0, f2(1.0f / 3.0f, 1.0f / 3.0f));
-                            Dw = __ffma2_rn(D1, f2(1.0f / 12.0f, 1.0f / 12.0f), Dw);
-                        }
-                        S[a] = __ffma2_rn(Dw, gsr, S[a]);
-                    }
-                }
-                float F[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)   // Korteweg force plus the body force rho g
-                    F[a] = __fmaf_rn(rho, p.g[a], -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y);
-                // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2, the node's omega
-                const float om = p.var_visc ? omega_var_f(p, rho) : p.omega;
-                const float pref = p.var_visc ? p.phi_sign * (1.0f - 0.5f * om) : p.phi_pref;
-                const float omw = p.var_visc ? 1.0f - om : p.omw;
-                const int gr0 = THREE ? ty + 1 : 0, gc0 = tx + 1;
-                float Phi[3];
-                Phi[0] = pref * 0.5f * (s_g[pc % GS][0][gr0][gc0 + 1] - s_g[pc % GS][0][gr0][gc0 - 1]);
-                Phi[1] = THREE ? pref * 0.5f *
-                                     (s_g[pc % GS][1][gr0 + 1][gc0] - s_g[pc % GS][1][gr0 - 1][gc0])
-                               : 0.0f;
-                Phi[2] = pref * 0.5f *
-                         (s_g[(pc + 1) % GS][2][gr0][gc0] - s_g[(pc - 1) % GS][2][gr0][gc0]);
-                // bare velocity and 1/rho of the node, formed by phase A from the same populations
-                const float4 uvn = sm.uv[pc & 3][ty][tx];
-                const float inv = uvn.w;
-                const float un[3] = {uvn.x, uvn.y, uvn.z};
-                // product-form factors, paired (equilibrium, extended)
-                float2 ES[3][3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (!THREE && a == 1) {
-                        ES[1][0] = ES[1][1] = ES[1][2] = f2(1.0f, 1.0f);
-                        continue;
-                    }
-                    const float ua = un[a];
-                    const float ze = 1.0f / 3.0f + ua * ua;
-                    const float xs = ua + F[a] * inv;
-                    const float zs = 1.0f / 3.0f + xs * xs + Phi[a] * inv;
-                    ES[a][0] = f2(0.5f * (ze - ua), 0.5f * (zs - xs));
-                    ES[a][1] = f2(1.0f - ze, 1.0f - zs);
-                    ES[a][2] = f2(0.5f * (ze + ua), 0.5f * (zs + xs));
-                }
-                float2 A[3][3];
-                const float2 rr = f2(rho, rho);
-#pragma unroll
-                for (int cx = 0; cx < 3; ++cx) {
-                    const float2 rx = __fmul2_rn(rr, ES[0][cx]);
-#pragma unroll
-                    for (int cy = 0; cy < 3; ++cy) A[cx][cy] = __fmul2_rn(rx, ES[1][cy]);
-                }
-                // post = f* + (1 - omega)(f - feq), pushed to r + c_i
-                const int X[3] = {wrapf(xi - 1, g.nx), xi, wrapf(xi + 1, g.nx)};
-                const int Y[3] = {THREE ? wrapf(yi - 1, g.ny) : 0, yi, THREE ? wrapf(yi + 1, g.ny) : 0};
-                const int Z[3] = {wrapf(zc - 1, g.nz), zc, wrapf(zc + 1, g.nz)};
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-                    const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
-                    const float post = SHIFT ? fmaf(fmaf(omw, fi[i] - es.x, es.y), inv, -weight_f<LAT>(i))
-                                             : fmaf(omw, fi[i] - es.x, es.y);
-                    const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
-                                         plane * (unsigned)Z[cz + 1];
-                    if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = from_f<ST>(post);
-                    else                   fout[i * N + dst] = from_f<ST>(post);
-                }
-            }
-        }
-    }
-}
-
-// FP32 populations; dynamic shared memory of sizeof(SharedF<LAT>).
-template <int LAT, bool MASK>
-__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
-k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
-           float *__restrict__ fout, int *__restrict__ status)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SharedF<LAT> &sm = *reinterpret_cast<SharedF<LAT> *>(smem_raw);
-    fused_tile<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm);
-}
-
-// Shifted 16-bit storage (ST = __half or __nv_bfloat16): populations h_i
-// with the source densities rho_src read and rho_dst written; dynamic shared
-// memory of sizeof(SharedS<LAT>).
-template <int LAT, typename ST>
-__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
-k_step_shifted(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
-               const float *__restrict__ rho_src, float *__restrict__ rho_dst,
-               int *__restrict__ status)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
-    fused_tile<LAT, false, ST, SharedS<LAT>>(g, p, nullptr, f, fout, status, blockIdx.x, blockIdx.y,
-                                            blockIdx.z, sm, rho_src, rho_dst);
-}
-
-// Many lattices of one type and one storage in one launch: descriptor of one
-// member for the current step parity, and the (member, tile) work items.
-struct MemberF {
-    GeoF g;
-    PhysF p;
-    const uint8_t *mask;   // nullptr when the member has no solid node
-    const void *src;       // float, or 16-bit shifted populations
-    void *dst;
-    const float *rho_src;  // shifted storage: densities of src and dst
-    float *rho_dst;
-    int *status;
-    int tiles_x, tiles_y;
-};
-
-struct WorkItem {
-    int member, bx, by, bz;
-};
-
-// Persistent: CTA b takes items b, b + gridDim.x, ... (a fixed assignment,
-// so each member's result does not depend on what else is in the batch);
-// dynamic shared memory of sizeof(SharedF<LAT>).
-template <int LAT>
-__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
-k_step_f32_batch(const MemberF *__restrict__ members, const WorkItem *__restrict__ items,
-                 int n_items)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SharedF<LAT> &sm = *reinterpret_cast<SharedF<LAT> *>(smem_raw);
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const WorkItem w = items[it];
-        const MemberF &m = members[w.member];
-        const float *src = static_cast<const float *>(m.src);
-        float *dst = static_cast<float *>(m.dst);
-        if (m.mask)
-            fused_tile<LAT, true>(m.g, m.p, m.mask, src, dst, m.status, w.bx, w.by, w.bz, sm);
-        else
-            fused_tile<LAT, false>(m.g, m.p, m.mask, src, dst, m.status, w.bx, w.by, w.bz, sm);
-        __syncthreads();   // the rings are reused by the next item
-    }
-}
-
-// The same over members with 16-bit shifted storage (no solid nodes);
-// dynamic shared memory of sizeof(SharedS<LAT>).
-template <int LAT, typename ST>
-__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
-k_step_shifted_batch(const MemberF *__restrict__ members, const WorkItem *__restrict__ items,
-                     int n_items)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const WorkItem w = items[it];
-        const MemberF &m = members[w.member];
-        fused_tile<LAT, false, ST, SharedS<LAT>>(m.g, m.p, nullptr, static_cast<const ST *>(m.src),
-                                                static_cast<ST *>(m.dst), m.status, w.bx, w.by,
-                                                w.bz, sm, m.rho_src, m.rho_dst);
-        __syncthreads();
-    }
-}
-
-}  // namespace lbmf
+#define LBMF_NS lbmf
+#define LBMF_ROWS 8
+#include "lbm_fused_f32_body.cuh"
+#undef LBMF_NS
+#undef LBMF_ROWS

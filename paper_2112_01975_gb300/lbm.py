@@ -62,6 +62,8 @@ def _load():
     L.lbm_time_kernels.argtypes = [vp, i64, dp]
     L.lbm_set_chunk.argtypes = [vp, C.c_int]
     L.lbm_autotune.argtypes = [vp, C.POINTER(C.c_int)]
+    L.lbm_get_tile.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lbm_set_tile.argtypes = [vp, C.c_int]
     L.lbm_reduce_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.lbm_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
     L.lbm_batch_step.argtypes = [vp, i64]
@@ -95,6 +97,8 @@ lbm_launch_count = _lib.lbm_launch_count
 lbm_time_kernels = _lib.lbm_time_kernels
 lbm_set_chunk = _lib.lbm_set_chunk
 lbm_autotune = _lib.lbm_autotune
+lbm_get_tile = _lib.lbm_get_tile
+lbm_set_tile = _lib.lbm_set_tile
 lbm_reduce_noalloc = _lib.lbm_reduce_noalloc
 lbm_batch_create = _lib.lbm_batch_create
 lbm_batch_step = _lib.lbm_batch_step
@@ -278,11 +282,22 @@ class LBM:
         self._check(_lib.lbm_set_chunk(self._h, int(chunk)))
 
     def autotune(self) -> int:
-        """Time the fused step's chunk candidates on the current state (which
-        is restored) and keep the fastest; returns it (0 for FP64)."""
+        """Time the fused step's chunk candidates (and, for D3Q27 FP32, the 8-
+        and 7-row tiles) on the current state (which is restored) and keep the
+        fastest; returns the chunk (0 for FP64)."""
         c = C.c_int()
         self._check(_lib.lbm_autotune(self._h, C.byref(c)))
         return c.value
+
+    def set_tile(self, tile_y: int):
+        """Tile height of the D3Q27 FP32 step: 8 (default) or 7 rows."""
+        self._check(_lib.lbm_set_tile(self._h, int(tile_y)))
+
+    def tile(self):
+        """(tile_x, tile_y) of the fused step in use; (0, 0) for FP64."""
+        x, y = C.c_int(), C.c_int()
+        self._check(_lib.lbm_get_tile(self._h, C.byref(x), C.byref(y)))
+        return x.value, y.value
 
     @property
     def launches(self) -> int:

@@ -161,6 +161,52 @@ def test_f32_chunking_and_graph_do_not_change_results(lbm):
         assert np.array_equal(outs[0], x)
 
 
+@pytest.mark.parametrize("shape,chunk,solid", [((64, 40, 48), 16, False), ((45, 37, 29), 7, True),
+                                              ((128, 128, 128), 32, False)])
+def test_f32_seven_row_tiles_do_not_change_results(lbm, shape, chunk, solid):
+    """32 x 7 tiles (ragged in y, with and without solids, and the 128^3
+    bench lattice at its one-wave chunk) give bitwise the populations of the
+    default 32 x 8 tiles, through graph replays and plain launches."""
+    w = inputs.DROP_D3Q27_128
+    nx, ny, nz = shape
+    mask = None
+    if solid:
+        mask = np.zeros(nx * ny * nz, dtype=np.uint8)
+        z = np.arange(nx * ny * nz) // (nx * ny)
+        mask[z == 0] = 1
+    g = lbm.LBM(1, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
+                storage=lbm.F32, mask=mask, rho_w=w.rho_v)
+    g.init(inputs.add_noise(inputs.drop(nx, ny, nz, nx / 5.0, w.rho_v, w.rho_l), 1e-4, 5))
+    g.set_chunk(chunk)
+    g.step(3)
+    f0 = g.get_populations()
+    assert g.tile() == (32, 8)
+    g.step(9)
+    f8 = g.get_populations()
+    g.set_populations(f0)
+    g.set_tile(7)
+    assert g.tile() == (32, 7)
+    g.step(8)                      # graph replays
+    g.step(1)                      # and a plain launch
+    assert np.array_equal(g.get_populations(), f8)
+
+
+def test_f32_tile_setter_rejects_other_cases(lbm):
+    w = inputs.DROP_D3Q27_128
+    g = lbm.LBM(1, 32, 16, 12, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b, storage=lbm.F32)
+    for bad in (6, 9, 0):
+        with pytest.raises(lbm.LBMError):
+            g.set_tile(bad)
+    h = lbm.LBM(1, 32, 16, 12, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b, storage=lbm.F16S)
+    with pytest.raises(lbm.LBMError):
+        h.set_tile(7)
+    assert h.tile() == (32, 8)
+    d = lbm.LBM(0, 64, 64, 1, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b, storage=lbm.F32)
+    assert d.tile() == (128, 1)
+    with pytest.raises(lbm.LBMError):
+        d.set_tile(7)
+
+
 def test_f32_population_io_roundtrip(lbm):
     import torch
     w = inputs.DROP_D2Q9_64
