@@ -89,6 +89,9 @@ def test_create_rejects_bad_arguments_without_a_device(lib, args):
 def test_null_handle_calls_are_errors(lib):
     assert lib.lbm_step(None, C.c_int64(1)) == 1
     assert lib.lbm_sync(None, -1) == 1
+    x, y = C.c_int(-1), C.c_int(-1)
+    assert lib.lbm_get_tile(None, C.byref(x), C.byref(y)) == 1 and x.value == -1
+    assert lib.lbm_set_tile(None, 7) == 1
     lib.lbm_last_error.restype = C.c_char_p
     assert lib.lbm_last_error(None) == b"null handle"
     lib.lbm_destroy(None)
