@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--workload", default="d3q27_drop_128^3_pr_tr0.7")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 7, 8],
+                    help="D3Q27 FP32 tile height (0: picked by the autotuner, or 8 with --chunk)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--mode", default="step", choices=["step", "serve", "validate"],
@@ -471,6 +473,8 @@ def main():
     if storage != F64:
         chunk = args.chunk or g.autotune()
         g.set_chunk(chunk)
+        if args.tile and storage == F32 and w.lattice == 1:
+            g.set_tile(args.tile)
     g.step(args.warmup)
     g.sync()
     with ClockSampler(local) as clocks:
