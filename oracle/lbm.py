@@ -22,7 +22,7 @@ EOS_VDW, EOS_PR, EOS_RKS, EOS_CS, EOS_SC1, EOS_SC2 = 0, 1, 2, 3, 4, 5
 # Default EOS constants (lattice units): van der Waals a = 9/49, b = 2/21;
 # Peng-Robinson and Redlich-Kwong-Soave a = 2/49, b = 2/21, acentric 0.344
 # (the paper's water value, Sec. 3.1); Carnahan-Starling a = 1, b = 4. The
-# Shan-Chen forms (Appendix C) take no a, b: their b here only bounds the
+# Shan-Chen forms (Appendix G) take no a, b: their b here only bounds the
 # density range the Maxwell tools search (rho < 1/b).
 DEFAULT_AB = {EOS_VDW: (9.0 / 49.0, 2.0 / 21.0), EOS_PR: (2.0 / 49.0, 2.0 / 21.0),
               EOS_RKS: (2.0 / 49.0, 2.0 / 21.0), EOS_CS: (1.0, 4.0),

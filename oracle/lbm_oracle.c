@@ -9,7 +9,7 @@
  * It follows the paper's steps in the paper's order, with naive loops over
  * all Q directions and no blocking, fusion or reordering:
  *   moments            Sec. 2.3.3, rho = sum f_i, rho u = sum c_i f_i
- *   equation of state  Sec. 3.1, Eqs. vdWEoS, PREoS, RKSEoS, CSEos; Appendix C,
+ *   equation of state  Sec. 3.1, Eqs. vdWEoS, PREoS, RKSEoS, CSEos; Appendix G,
  *                      Eqs. SCeos, SC1, SC2 (Shan-Chen)
  *   pseudo-potential   Sec. 2.3.4, psi = sqrt|P - P0|, P0 = rho/3 (end of Sec. 2.3.5)
  *   Korteweg force     Eq. Kforce_final with w_i of Eq. wi, plus an optional
@@ -132,7 +132,7 @@ double oracle_eos_RTc(int eos, double a, double b)
     case 1: return (0.0778 / 0.45724) * a / b;
     case 2: return (0.08664 / 0.42748) * a / b;
     case 3: return (0.18727 / 0.4963) * a / b;
-    case 4: return -4.0;              /* critical coupling G_c of Eq. SC1 (Appendix C) */
+    case 4: return -4.0;              /* critical coupling G_c of Eq. SC1 (Appendix G) */
     case 5: return -exp(2.0);         /* critical coupling G_c of Eq. SC2 */
     }
     return NAN;
@@ -169,7 +169,7 @@ static long node_at(const oracle_ctx *o, long x, long y, long z)
  * then the kinematic viscosity nu = (tau - 1/2)/3 goes linearly in rho from
  * its liquid value at rho_l (the tau of oracle_create) to its vapour value
  * at rho_v (tau_v), held constant beyond them (the paper sets a vapour to
- * liquid viscosity ratio, Sec. 6, without stating the interpolation). */
+ * liquid viscosity ratio, Sec. 5.2, without stating the interpolation). */
 static double omega_at(const oracle_ctx *o, double rho)
 {
     if (!(o->tau_v > 0.0)) return o->omega;

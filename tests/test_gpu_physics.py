@@ -132,7 +132,7 @@ def test_rks_and_cs_parity_and_coexistence(lbm, eos, a0, b):
 
 @pytest.mark.parametrize("eos", [4, 5])
 def test_shan_chen_parity_coexistence_and_fp32(lbm, eos):
-    """Both Shan-Chen forms (Appendix C) at T/Tc = 0.9, width 4: FP64 matches
+    """Both Shan-Chen forms (Appendix G) at T/Tc = 0.9, width 4: FP64 matches
     the oracle to 1e-10 after 300 steps, relaxes to the Maxwell densities
     (1 %), and FP32 storage holds them within 0.5 % of FP64."""
     tr = 0.9

@@ -1,5 +1,5 @@
 """Density-dependent relaxation time (the vapour/liquid viscosity ratio of
-the paper's Sec. 6 and of Sec. 4.1 configuration (b)) on the GPU.
+the paper's Sec. 5.2 and of Sec. 4.1 configuration (b)) on the GPU.
 
 - Parity with the oracle, FP64 to 1e-10 and FP32 at its storage tolerance,
   on a D2Q9 and a D3Q27 drop with tau_v != tau.

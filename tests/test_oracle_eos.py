@@ -1,7 +1,7 @@
 """Pins of the oracle's equations of state and of the host-side closed forms.
 
 Critical points and critical compressibilities are textbook values of each
-EOS (Sec. 3.1), and for the Shan-Chen forms the values Appendix C prints; the van der Waals Maxwell construction is checked with the
+EOS (Sec. 3.1), and for the Shan-Chen forms the values Appendix G prints; the van der Waals Maxwell construction is checked with the
 closed-form antiderivative of P/rho^2, not with the quadrature the tool uses.
 """
 import math
@@ -51,7 +51,7 @@ def test_critical_compressibility(eos, zc):
 @pytest.mark.parametrize("eos,gc,rc", [(4, -4.0, math.log(2.0)), (5, -math.exp(2.0), 1.0)])
 def test_shan_chen_critical_points(eos, gc, rc):
     """The critical couplings and densities the paper prints for the two
-    Shan-Chen pseudo-potentials (Appendix C: G_c = -4, rho_c = 0.6931 and
+    Shan-Chen pseudo-potentials (Appendix G: G_c = -4, rho_c = 0.6931 and
     G_c = -7.389, rho_c = 1): at T/Tc = 1 the coupling is G_c and P' = P'' = 0
     at rho_c, and nowhere else does P' vanish."""
     e = EOS(eos, 1.0)
@@ -69,7 +69,7 @@ def test_shan_chen_critical_points(eos, gc, rc):
 
 @pytest.mark.parametrize("eos", [4, 5])
 def test_shan_chen_sound_faster_in_vapour(eos):
-    """The paper's remark on the Shan-Chen forms (Appendix C): at coexistence
+    """The paper's remark on the Shan-Chen forms (Appendix G): at coexistence
     the isothermal sound speed dP/drho is larger in the vapour than in the
     liquid, the reverse of the cubic equations of state."""
     e = EOS(eos, 0.8)
@@ -134,7 +134,7 @@ def test_width_scales_as_sqrt_kappa_over_a():
 
 
 @pytest.mark.parametrize("w", [inputs.DROP_D2Q9_64, inputs.DROP_D3Q27_128,
-                               inputs.COALESCENCE_D3Q27_256])
+                               inputs.COALESCENCE_D3Q27_256, inputs.IMPACT_D3Q27_384])
 def test_workload_constants_match_maxwell(w):
     """The stored init densities and kappa of each workload come from the EOS."""
     e = EOS(w.eos, w.t_over_tc, a=w.a, b=w.b)
