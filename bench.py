@@ -1,13 +1,17 @@
 """Throughput of the two-phase lattice Boltzmann step on GB300.
 
-Workload: D3Q27 static drop, 128^3 periodic, Peng-Robinson EOS at T/Tc = 0.7,
-drop radius 24 (seeded synthetic init, see paper_2112_01975_gb300/inputs.py),
-FP32 storage with the fused FP32 step by default; the FP64 path is timed on
-the same workload and reported under "f64". One bench step = one lattice
-time step over all 128^3 nodes (moments, EOS, Korteweg force, correction,
-collision, streaming). Metric: MLUPS (million lattice-node updates per
-second), whole job. The population buffers (2 x 226 MB in FP32, 2 x 453 MB in
-FP64) exceed the 129 MB L2, so no flush is needed between steps.
+Workload (default): D3Q27 drop impact on a textured wall, 384x384x256, a wall
+at z = 0 with 8x8x16 pillars at pitch 16 (halfway bounce-back, solid density
+rho_v), Peng-Robinson EOS at T/Tc = 0.5 (density ratio 1.1e4), a drop of
+radius 60 moving down at U = 0.05 (seeded synthetic init, see
+paper_2112_01975_gb300/inputs.py), FP32 storage with the fused FP32 step; the
+FP64 path is timed on the same workload and reported under "f64". One bench
+step = one lattice time step over all 37.7 M nodes (moments, EOS, Korteweg
+force, correction, collision, streaming with bounce-back). Metric: MLUPS
+(million lattice-node updates per second), whole job. The population buffers
+(2 x 4.08 GB in FP32) exceed the 129 MB L2, so no flush is needed between
+steps. ``--workload`` selects another configured workload (the 128^3 drop,
+the 256^3 coalescence).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -50,19 +54,48 @@ COLLIDE_FP64_FLOPS_PER_NODE = 482
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (an FMA-chain probe measured 1.19)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per lattice node
+# of one launch of the fused step, from an ncu capture of the named workload
+# (scaled to the capture's lattice, as stated), keyed by (workload, storage,
+# tile rows, warp-specialised); each entry records the SHA-256 prefix of the fused kernel's
+# source it was taken on, and is not used once that source has changed.
+MEASURED_TRAFFIC = {}
+FUSED_SRC = os.path.join(ROOT, "paper_2112_01975_gb300", "csrc", "lbm_fused_f32_body.cuh")
+
+
+def fused_src_sha() -> str:
+    import hashlib
+    with open(FUSED_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_traffic(name: str, storage: str, rows: int, ws: bool, nodes: int):
+    """ncu DRAM bytes of one launch scaled to `nodes`, or None."""
+    v = MEASURED_TRAFFIC.get((name, storage, rows, ws))
+    if v is None or v["src_sha"] != fused_src_sha():
+        return None
+    return v["bytes_per_node"] * nodes
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="d3q27_drop_128^3_pr_tr0.7")
+    ap.add_argument("--workload", default="d3q27_impact_384x384x256_pr_tr0.5")
+    ap.add_argument("--shape", default="",
+                    help="nx,ny,nz: run the workload scaled to this lattice (profiling captures)")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16s", "bf16s"])
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 7, 8],
                     help="D3Q27 FP32 tile height (0: picked by the autotuner, or 8 with --chunk)")
+    ap.add_argument("--ws", type=int, default=-1, choices=[-1, 0, 1],
+                    help="FP32 warp-specialised kernel (-1: picked by the autotuner, or plain with --chunk)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving sweep reported under \"serve\"")
     ap.add_argument("--mode", default="step", choices=["step", "serve", "validate"],
                     help="serve: the parameter-sweep server against one-at-a-time FP64; "
                          "validate: the coexistence/Laplace, coalescence and impact runs "
@@ -170,46 +203,62 @@ def host_cpu() -> dict:
     return {"cpu": model, "nproc": os.cpu_count()}
 
 
-def oracle_sample_mlups(w, target_s: float = 12.0, openmp: bool = False):
-    """FP64 oracle throughput on the workload scaled to 48^3 (64^2 in 2D): one
-    host thread, or (openmp) the -fopenmp build of the same source on all cores."""
+def sample_shape(w, kind: str):
+    """Lattice of the CPU oracle's bounded sample of workload w: the
+    all-host-cores and one-thread baselines ("cpu") and the reference arm,
+    whose every step is one lattice update of it ("reference")."""
+    if w.lattice == 0:
+        return (64, 64, 1)
+    if w.mask_seed is not None:   # the impact keeps its pillars and gap: a 1/4 or 1/6 box
+        return (96, 96, 64) if kind == "cpu" else (48, 48, 40)
+    return (48, 48, 48) if kind == "cpu" else (32, 32, 32)
+
+
+def oracle_for(w, shape, openmp: bool = False):
+    """The FP64 oracle on workload w scaled to shape, initialised."""
     from oracle.lbm import OracleLBM
-    n = 48 if w.lattice == 1 else 64
-    nz = n if w.lattice == 1 else 1
-    rho = w.rho0_scaled(n)
-    o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
-                  openmp=openmp)
-    o.init(rho)
+    rho, u0, mask = w.fields(shape)
+    nx, ny, nz = shape
+    o = OracleLBM(w.lattice, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, w.tau, mask=mask, a=w.a,
+                  b=w.b, rho_w=1.0 if w.rho_w is None else w.rho_w, openmp=openmp)
+    o.init(rho, u0)
+    return o
+
+
+def oracle_sample_mlups(w, target_s: float = 12.0, openmp: bool = False):
+    """FP64 oracle throughput on the workload scaled down (sample_shape): one
+    host thread, or (openmp) the -fopenmp build of the same source on all cores."""
+    shape = sample_shape(w, "cpu")
+    o = oracle_for(w, shape, openmp=openmp)
     o.step(1)
     steps, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < target_s:
         o.step(1)
         steps += 1
     dt = time.perf_counter() - t0
-    return n * n * nz * steps / dt / 1e6, (f"the workload scaled to {n}x{n}x{nz} (radius and drop "
-                                           f"centres x {n}/{w.nx}), {steps} steps, {dt:.1f} s")
+    nodes = shape[0] * shape[1] * shape[2]
+    return nodes * steps / dt / 1e6, (f"the workload scaled to {shape[0]}x{shape[1]}x{shape[2]} "
+                                      f"(drop radius and centres x {shape[0]}/{w.nx}), {steps} "
+                                      f"steps, {dt:.1f} s")
 
 
 def run_reference(args, w, world, rank):
     """The CPU oracle as it stands, one host thread, each step one lattice
-    update of the workload scaled to 32^3 (3D) or 64^2 (2D)."""
+    update of the workload scaled down (sample_shape)."""
     if rank != 0:
         return
-    from oracle.lbm import OracleLBM
-    n = 32 if w.lattice == 1 else 64
-    nz = n if w.lattice == 1 else 1
-    rho = w.rho0_scaled(n)
-    o = OracleLBM(w.lattice, n, n, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b)
-    o.init(rho)
+    shape = sample_shape(w, "reference")
+    o = oracle_for(w, shape)
     for _ in range(args.warmup):
         o.step(1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         o.step(1)
     dt = time.perf_counter() - t0
-    mlups = n * n * nz * args.steps / dt / 1e6
-    sample = (f"{w.name} scaled to {n}x{n}x{nz} (radius and drop centres x {n}/{w.nx}), "
-              "one lattice update per step")
+    nodes = shape[0] * shape[1] * shape[2]
+    mlups = nodes * args.steps / dt / 1e6
+    sample = (f"{w.name} scaled to {shape[0]}x{shape[1]}x{shape[2]} (drop radius and centres x "
+              f"{shape[0]}/{w.nx}), one lattice update per step")
     print(json.dumps({
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -264,23 +313,23 @@ def timed_steps(g, stream, steps, dist, local):
     return ms, l1 - l0
 
 
-def run_serve(args):
-    """Sweep of Poisson-arriving drop solves (rate 50/s): continuous-batching
-    server (each request FP32 or FP16-shifted, drawn per request) vs the same
-    requests solved one at a time in FP64."""
-    import __graft_entry__
-    __graft_entry__.build()
-    import torch
-    from paper_2112_01975_gb300 import serve
-    torch.cuda.set_device(0)
-    reqs = serve.sweep_requests(count=args.requests, rate=50.0, seed=5, steps=args.request_steps)
-    prepared = {r.rid: serve.setup(r) for r in reqs}        # host set-up, not timed
-    srv = serve.Server(hbm_budget=64 << 30, tick_steps=100)
-    fast = serve.summarize(srv.run(reqs, prepared, realtime=True))
-    slow = serve.summarize(serve.run_sequential_f64(reqs, prepared, realtime=True))
-    lu = sum(r.nodes * r.steps for r in reqs)
-    print(json.dumps({
-        "mode": "serve", "metric": "sweep solves/s, p50/p99 latency", "unit": "solves/s",
+def serve_sweep(count: int, request_steps: int, seed: int = 5) -> dict:
+    """Sweep of Poisson-arriving drop solves (rate 50/s): the continuous-
+    batching server (each request FP32 or FP16-shifted, drawn per request)
+    against the same requests solved one at a time in FP64. Each request's
+    host set-up (EOS values from a table built once per arm, the initial
+    density field) runs after its arrival and counts in its latency."""
+    from paper_2112_01975_gb300 import eos_tables, serve
+    reqs = serve.sweep_requests(count=count, rate=50.0, seed=seed, steps=request_steps)
+    t = time.perf_counter()
+    trs = [r.t_over_tc for r in reqs]
+    table = eos_tables.SetupTable(0, min(trs), max(trs))
+    t_table = time.perf_counter() - t
+    srv = serve.Server(hbm_budget=64 << 30, tick_steps=50)
+    fast = serve.summarize(srv.run(reqs, realtime=True, table=table))
+    slow = serve.summarize(serve.run_sequential_f64(reqs, realtime=True, table=table))
+    return {
+        "metric": "sweep solves/s, p50/p99 latency", "unit": "solves/s",
         "value": fast["solves_per_s"], "higher_is_better": True,
         "server_batched_f32_f16s": fast, "sequential_fp64": slow,
         "speedup_solves_per_s": fast["solves_per_s"] / slow["solves_per_s"],
@@ -289,10 +338,23 @@ def run_serve(args):
                                "64..192^3, T/Tc U[0.5, 0.95], radius U[0.15, 0.35] n, "
                                "Poisson arrivals 50/s, storage FP32 or FP16-shifted "
                                "with probability 1/2, interface width 5, rest start",
-                   "requests": args.requests, "steps_per_request": args.request_steps,
-                   "lattice_updates": lu, "tick_steps": 100, "hbm_budget_gib": 64,
-                   "peak_resident": srv.peak_resident},
-        "data": "synthetic"}), flush=True)
+                   "requests": count, "steps_per_request": request_steps,
+                   "lattice_updates": sum(r.nodes * r.steps for r in reqs),
+                   "tick_steps": 50, "hbm_budget_gib": 64,
+                   "peak_resident": srv.peak_resident, "batches_built": srv.batches_built,
+                   "latency": "arrival to result on the host, set-up included",
+                   "setup_table_s": t_table}}
+
+
+def run_serve(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    torch.cuda.set_device(0)
+    out = serve_sweep(args.requests, args.request_steps)
+    out["mode"] = "serve"
+    out["data"] = "synthetic"
+    print(json.dumps(out), flush=True)
 
 
 def _validate_cfg2(L, storage, tr, steps):
@@ -465,87 +527,105 @@ def main():
     stream = torch.cuda.Stream()
     from paper_2112_01975_gb300.lbm import BF16S, F16S
     storage = {"f64": F64, "f32": F32, "f16s": F16S, "bf16s": BF16S}[args.storage]
-    g = LBM(w.lattice, w.nx, w.ny, w.nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
-            stream=stream, storage=storage)
-    rho0 = w.rho0()
-    g.init(rho0)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (w.nx, w.ny, w.nz)
+    nx, ny, nz = shape
+    nodes = nx * ny * nz
+    rho0, u0, mask = w.fields(shape)
+    D = 3 if w.lattice else 2
+
+    def make(st):
+        return LBM(w.lattice, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, w.tau, mask=mask, a=w.a,
+                   b=w.b, rho_w=w.rho_w, stream=stream, storage=st)
+
+    g = make(storage)
+    g.init(rho0, u0)
     chunk = 0
     if storage != F64:
         chunk = args.chunk or g.autotune()
         g.set_chunk(chunk)
         if args.tile and storage == F32 and w.lattice == 1:
             g.set_tile(args.tile)
+        if args.ws >= 0 and storage == F32:
+            g.set_warp_specialized(bool(args.ws))
     g.step(args.warmup)
     g.sync()
     with ClockSampler(local) as clocks:
         ms, launches = timed_steps(g, stream, args.steps, dist, local)
-    mlups = job_mlups(w.nodes, args.steps, world, ms)
+    mlups = job_mlups(nodes, args.steps, world, ms)
 
-    # per-kernel durations (plain launches with events between kernels)
+    # The dominant kernel's average launch duration over the timed region:
+    # the replayed graph launches one fused kernel per step (FP32 and
+    # shifted storage), so it is the timed region's length over its
+    # launches. Plain launches with events between kernels give a second
+    # figure (and the FP64 path's split into its two kernels).
     n_t = max(5, min(50, args.steps // 4))
     ms_macro, ms_collide = g.time_kernels(n_t)
     peak, peak_kind = measured_peaks()
-    alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * w.nodes
-    achieved = alg / (ms_collide * 1e-3) / 1e9
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
-    # fused step on this 128^3 workload (FP32: 262.5 + 186.8 MB; FP16
-    # shifted: 137.7 + 81.8 MB)
+    alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * nodes
+    per_step = launches / args.steps if args.steps else 1
     tile = g.tile()
-    traffic_fused = {("f32", 8): 449.34e6, ("f16s", 8): 219.49e6}.get((args.storage, tile[1])) \
-        if w.name == "d3q27_drop_128^3_pr_tr0.7" else None
+    ws = storage == F32 and g.warp_specialized
     if storage != F64:
+        ms_launch = ms / max(launches, 1)
+        achieved = alg / (ms_launch * 1e-3) / 1e9
+        traffic = measured_traffic(w.name, args.storage, tile[1], ws, nodes) if per_step == 1 else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic_fused,
+                    "frac": achieved / peak, "traffic": traffic,
                     "frac_of_nominal_7900_gbs": achieved / 7900.0,
-                    "kernel": "k_step_f32 (fused step)" if storage == F32 else "k_step_shifted",
-                    "peak_source": peak_kind + " hbm_gbs",
-                    "alg_bytes_per_launch": alg, "ms_per_launch": ms_collide,
+                    "kernel": ("k_step_f32_ws (fused step, warp-specialised)" if ws else
+                               "k_step_f32 (fused step)") if storage == F32 else "k_step_shifted",
+                    "peak_source": peak_kind + " hbm_gbs (burst copy)",
+                    "alg_bytes_per_launch": alg, "ms_per_launch": ms_launch,
+                    "ms_per_launch_source": "CUDA events over the timed graph replays / launches",
+                    "ms_per_launch_plain": ms_collide,
                     "chunk": chunk, "tile": f"{tile[0]}x{tile[1]}"}
     else:
-        tflops = COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (ms_collide * 1e-3) / 1e12
+        achieved = alg / (ms_collide * 1e-3) / 1e9
+        tflops = COLLIDE_FP64_FLOPS_PER_NODE * nodes / (ms_collide * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                    "traffic": 402.63e6 * w.nodes / 884736 if w.lattice == 1 else None,
+                    "traffic": None,
                     "kernel": "k_collide (FP64)",
                     "peak_source": "nominal FP64 rate of GB300 (recipe table)",
                     "flops_per_node": COLLIDE_FP64_FLOPS_PER_NODE,
                     "ms_per_launch": ms_collide, "ms_moments_kernel": ms_macro,
                     "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
 
-    # end to end through the C ABI with pinned host buffers
-    D = 3 if w.lattice else 2
+    # end to end through the C ABI with pinned host buffers: the initial
+    # density (and velocity) in, K steps, the density and velocity out
     pin_rho0 = torch.from_numpy(rho0).pin_memory()
-    out_rho = torch.empty(w.nodes, dtype=torch.float64).pin_memory()
-    out_u = torch.empty(D * w.nodes, dtype=torch.float64).pin_memory()
+    pin_u0 = torch.from_numpy(u0).pin_memory() if u0 is not None else None
+    out_rho = torch.empty(nodes, dtype=torch.float64).pin_memory()
+    out_u = torch.empty(D * nodes, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    g.init(pin_rho0.numpy())
+    g.init(pin_rho0.numpy(), None if pin_u0 is None else pin_u0.numpy())
     g.step(args.steps)
     g._check(_lib.lbm_moments(g._h, ctypes.c_void_p(out_rho.data_ptr()),
                               ctypes.c_void_p(out_u.data_ptr()), None, 0))
     t_e2e = reduce_max(time.perf_counter() - t0, dist, "cuda")
-    e2e_mlups = job_mlups(w.nodes, args.steps, world, t_e2e * 1e3)
+    e2e_mlups = job_mlups(nodes, args.steps, world, t_e2e * 1e3)
+    h2d = 8 * nodes * (1 + (D if u0 is not None else 0))
 
     # the FP64 path on the same workload, reported beside the headline
     f64 = None
     if storage == F32 and not args.no_f64:
         g.close()
         del g
-        h = LBM(w.lattice, w.nx, w.ny, w.nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
-                stream=stream, storage=F64)
-        h.init(rho0)
+        h = make(F64)
+        h.init(rho0, u0)
         h.step(5)
         k64 = max(20, args.steps // 10)
         ms64, _ = timed_steps(h, stream, k64, dist, local)
         m64, c64 = h.time_kernels(10)
-        f64 = {"value": w.nodes * k64 * world / (ms64 * 1e-3) / 1e6, "unit": "MLUPS",
+        f64 = {"value": nodes * k64 * world / (ms64 * 1e-3) / 1e6, "unit": "MLUPS",
                "steps": k64, "ms_per_step": ms64 / k64,
                "roofline": {"bound": "alu", "kernel": "k_collide (FP64)",
-                            "achieved": COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (c64 * 1e-3) / 1e12,
+                            "achieved": COLLIDE_FP64_FLOPS_PER_NODE * nodes / (c64 * 1e-3) / 1e12,
                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": COLLIDE_FP64_FLOPS_PER_NODE * w.nodes / (c64 * 1e-3) / 1e12
+                            "frac": COLLIDE_FP64_FLOPS_PER_NODE * nodes / (c64 * 1e-3) / 1e12
                             / FP64_PEAK_TFLOPS,
                             "ms_per_launch": c64, "ms_moments_kernel": m64}}
         h.close()
@@ -554,6 +634,12 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    serve_line = None
+    if world == 1 and not args.no_serve:
+        if f64 is None:
+            g.close()
+        torch.cuda.empty_cache()
+        serve_line = serve_sweep(args.requests, args.request_steps)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, sample = oracle_sample_mlups(w)
@@ -571,21 +657,24 @@ def main():
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": w.name, "lattice": "D3Q27" if w.lattice else "D2Q9",
-                   "nodes": w.nodes, "storage": args.storage,
+        "config": {"workload": w.name if not args.shape else f"{w.name} scaled to {args.shape}",
+                   "lattice": "D3Q27" if w.lattice else "D2Q9", "shape": [nx, ny, nz],
+                   "nodes": nodes, "storage": args.storage,
                    "eos": "Peng-Robinson" if w.eos == 1 else "vdW",
+                   "solid_nodes": int(mask.sum()) if mask is not None else 0,
                    "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (
                        (27 if w.lattice else 9) * {"f64": 8, "f32": 4}.get(args.storage, 2)
-                       * w.nodes / 1e6),
+                       * nodes / 1e6),
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS",
-                "h2d_bytes_per_step": 8 * w.nodes / args.steps,
-                "d2h_bytes_per_step": 8 * (1 + D) * w.nodes / args.steps},
+                "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": 8 * (1 + D) * nodes / args.steps},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "f64": f64,
+        "serve": serve_line,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

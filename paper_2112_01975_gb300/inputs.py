@@ -138,34 +138,68 @@ class Workload:
     noise: float = 1e-4
     steps: int = 1000
     centres: tuple = ()   # several drops of the same radius; empty: one drop at the centre
+    # impact on a textured wall: pillar mask of this seed (None: no solid),
+    # the drop's lowest point `gap` nodes above the pillar tops, moving down
+    # at u_down in the liquid (scaled by the liquid fraction in the interface)
+    mask_seed: int | None = None
+    gap: float = 8.0
+    u_down: float = 0.0
+    pillar: tuple = (8, 16, 16)   # side, height, pitch
 
     @property
     def nodes(self) -> int:
         return self.nx * self.ny * self.nz
 
-    def rho0(self) -> np.ndarray:
-        if self.centres:
-            r = drops(self.nx, self.ny, self.nz, list(self.centres), self.radius, self.rho_v,
-                      self.rho_l)
+    @property
+    def rho_w(self) -> float | None:
+        """Virtual density of solid nodes: the vapour's (non-wetting)."""
+        return self.rho_v if self.mask_seed is not None else None
+
+    def fields(self, shape=None):
+        """(rho0, u0, mask) on the workload's lattice, or on ``shape`` = (nx,
+        ny, nz) with the drop radius and centres scaled by nx' / nx (pillars
+        and the gap above them keep their size); the same noise amplitude and
+        seed. u0 is None for a start at rest, mask None without solids."""
+        nx, ny, nz = shape if shape is not None else (self.nx, self.ny, self.nz)
+        s = nx / self.nx
+        R = self.radius * s
+        mask = None
+        if self.mask_seed is not None:
+            side, height, pitch = self.pillar
+            mask = pillar_mask(nx, ny, nz, side=side, height=height, pitch=pitch,
+                               seed=self.mask_seed)
+            c = (nx // 2, ny // 2, height + R + self.gap)
+            r = drop(nx, ny, nz, R, self.rho_v, self.rho_l, center=c)
+        elif self.centres:
+            r = drops(nx, ny, nz, [tuple(v * s for v in cc) for cc in self.centres], R,
+                      self.rho_v, self.rho_l)
         else:
-            r = drop(self.nx, self.ny, self.nz, self.radius, self.rho_v, self.rho_l)
-        return add_noise(r, self.noise, self.seed)
+            r = drop(nx, ny, nz, R, self.rho_v, self.rho_l)
+        if self.noise:
+            r = add_noise(r, self.noise, self.seed)
+        u0 = None
+        if self.u_down:
+            u0 = np.zeros(3 * r.size)
+            frac = (r - self.rho_v) / (self.rho_l - self.rho_v)
+            u0[2 * r.size:] = -self.u_down * frac
+        if mask is not None:
+            r = np.where(mask == 1, self.rho_v, r)
+            if u0 is not None:
+                u0[2 * r.size:][mask == 1] = 0.0
+        return r, u0, mask
+
+    def rho0(self) -> np.ndarray:
+        return self.fields()[0]
 
     def rho0_scaled(self, n: int) -> np.ndarray:
         """The same layout on an n^3 (3D) or n^2 (2D) lattice: radius and
         drop centres scaled by n / nx; the same noise amplitude and seed."""
-        s = n / self.nx
-        nz = n if self.lattice == 1 else 1
-        if self.centres:
-            r = drops(n, n, nz, [tuple(c * s for c in cc) for cc in self.centres], self.radius * s,
-                      self.rho_v, self.rho_l)
-        else:
-            r = drop(n, n, nz, self.radius * s, self.rho_v, self.rho_l)
-        return add_noise(r, self.noise, self.seed)
+        return self.fields((n, n, n if self.lattice == 1 else 1))[0]
 
     def u0(self) -> np.ndarray:
         d = 2 if self.lattice == 0 else 3
-        return np.zeros(d * self.nodes)
+        u = self.fields()[1]
+        return np.zeros(d * self.nodes) if u is None else u
 
 
 # The EOS attraction parameter a is the named one scaled down by corresponding
@@ -202,5 +236,18 @@ COALESCENCE_D3Q27_256 = Workload("d3q27_coalescence_256^3_pr_tr0.45", 1, 256, 25
                                  radius=40.0, seed=3, a=0.00162040657246882, b=2.0 / 21.0,
                                  steps=10000, centres=((88.0, 128.0, 128.0), (168.0, 128.0, 128.0)))
 
+# D3Q27 drop impact on a textured wall, 384x384x256: wall at z = 0 plus
+# 8x8x16 square pillars at pitch 16 (lattice offset from seed 4), solid
+# density rho_w = rho_v (non-wetting); Peng-Robinson (b = 2/21, a scaled for
+# a liquid dP/drho of 0.1) at T/Tc = 0.5 (Maxwell density ratio 1.1e4); a
+# drop of radius 60 whose lowest point is 8 nodes above the pillar tops,
+# moving down at U = 0.05 in the liquid (We = rho_l U^2 2R / sigma = 19),
+# tau = 0.725, no noise. The largest single-GPU workload; FP32 storage.
+IMPACT_D3Q27_384 = Workload("d3q27_impact_384x384x256_pr_tr0.5", 1, 384, 384, 256, 1, 0.5,
+                            kappa=0.011670519231996029, tau=0.725,
+                            rho_v=0.000832893711960915, rho_l=9.219284708837831,
+                            radius=60.0, seed=4, a=0.00216512412385399, b=2.0 / 21.0,
+                            noise=0.0, steps=20000, mask_seed=4, u_down=0.05)
+
 WORKLOADS = {w.name: w for w in (DROP_D2Q9_64, DROP_D3Q27_128, DROP_D3Q27_96,
-                                 COALESCENCE_D3Q27_256)}
+                                 COALESCENCE_D3Q27_256, IMPACT_D3Q27_384)}

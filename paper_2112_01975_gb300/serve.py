@@ -6,13 +6,20 @@ every admitted lattice resident on the GPU, admits waiting requests in
 arrival order as soon as their device-memory footprint fits the budget, and
 advances all resident lattices of one lattice type and storage together with
 one batched launch per step (lbm_batch_*), in ticks of a fixed number of
-steps. A lattice that has finished its steps
-is read back and freed at the end of its tick, which frees room for the
-next arrivals. Every step of every solve runs in the library's kernels; a
-member of a batch evolves bitwise as it would alone.
+steps; a group's batch (its descriptors and captured graph) is kept from
+tick to tick while its members do not change. A lattice that has finished
+its steps is read back and freed at the end of its tick, which frees room
+for the next arrivals. Every step of every solve runs in the library's
+kernels; a member of a batch evolves bitwise as it would alone.
+
+Latency runs from a request's arrival to its result on the host and
+includes its host set-up: the EOS values (from a table built once when the
+server starts, eos_tables.SetupTable) and the initial density field. The
+host prepares arrived requests while the GPU runs a tick.
 
 The one-at-a-time FP64 baseline solves the same requests in arrival order,
-each alone on the GPU with FP64 storage.
+each alone on the GPU with FP64 storage, with the same set-up (the next
+arrived request is prepared while the current one runs).
 """
 from __future__ import annotations
 
@@ -56,6 +63,7 @@ class Result:
     mass: float
     digest: str           # sha1 of the final populations ("" unless asked for)
     failed: bool = False  # a density became non-finite; the solve was dropped
+    rho: np.ndarray | None = None   # the final density field, when kept
 
 
 def sweep_requests(count: int = 512, rate: float = 50.0, seed: int = 5, steps: int = 5000,
@@ -81,13 +89,17 @@ def sweep_requests(count: int = 512, rate: float = 50.0, seed: int = 5, steps: i
     return reqs
 
 
-def setup(req: Request, width: float = 5.0):
+def setup(req: Request, width: float = 5.0, table=None):
     """EOS parameters and the initial density of a request (van der Waals,
     attraction scaled for a liquid dP/drho of 0.1, interface width 5); the
-    lattice starts at rest in the physical velocity (lbm_init)."""
-    a = eos_tables.stable_a(0, req.t_over_tc)
-    rv, rl, _ = eos_tables.coexistence(0, req.t_over_tc, a)
-    kappa = eos_tables.kappa_for_width(0, req.t_over_tc, a, width=width)
+    lattice starts at rest in the physical velocity (lbm_init). table: an
+    eos_tables.SetupTable of the EOS and width, else computed directly."""
+    if table is not None:
+        a, rv, rl, kappa = table(req.t_over_tc)
+    else:
+        a = eos_tables.stable_a(0, req.t_over_tc)
+        rv, rl, _ = eos_tables.coexistence(0, req.t_over_tc, a)
+        kappa = eos_tables.kappa_for_width(0, req.t_over_tc, a, width=width)
     tau = 0.8 if req.oscillating else 1.0
     n = req.n
     nz = n if req.lattice == D3Q27 else 1
@@ -119,13 +131,13 @@ def _failed(req: Request, t0: float) -> Result:
                   float("nan"), "", failed=True)
 
 
-def _finish(req: Request, g: LBM, t0: float, digest: bool = False) -> Result:
+def _finish(req: Request, g: LBM, t0: float, digest: bool = False, keep: bool = False) -> Result:
     rho = g.moments()[0]
     mass, _ = g.reduce()
     digest = hashlib.sha1(g.get_populations().tobytes()).hexdigest() if digest else ""
     done = time.perf_counter() - t0
     return Result(req.rid, req.arrival, done, done - req.arrival, float(rho.min()),
-                  float(rho.max()), mass, digest)
+                  float(rho.max()), mass, digest, rho=rho if keep else None)
 
 
 def _open(req: Request, storage: int, prepared) -> LBM:
@@ -137,20 +149,63 @@ def _open(req: Request, storage: int, prepared) -> LBM:
     return g
 
 
+class _Preparer:
+    """Host set-up of requests that have arrived, once each, in arrival
+    order; given set-ups (a dict rid -> setup) are used as they are."""
+
+    def __init__(self, requests, table, given=None):
+        self.order = sorted(requests, key=lambda r: r.arrival)
+        self.table = table
+        self.done = dict(given or {})
+        self.k = 0
+
+    def __getitem__(self, rid):
+        return self.done[rid]
+
+    def prepare(self, req):
+        if req.rid not in self.done:
+            self.done[req.rid] = setup(req, table=self.table)
+
+    def prepare_arrived(self, now: float, realtime: bool, limit: int = 1 << 30):
+        """Set up arrived requests not yet prepared (at most limit of them)."""
+        while self.k < len(self.order) and limit > 0:
+            req = self.order[self.k]
+            if realtime and req.arrival > now:
+                break
+            if req.rid not in self.done:
+                self.prepare(req)
+                limit -= 1
+            self.k += 1
+
+
+def _table_for(requests, table):
+    if table is not None:
+        return table
+    trs = [r.t_over_tc for r in requests]
+    return eos_tables.SetupTable(0, min(trs), max(trs))
+
+
 class Server:
     """Continuous batching with admission by device-memory footprint."""
 
-    def __init__(self, hbm_budget: int, tick_steps: int = 250, digest: bool = False):
+    def __init__(self, hbm_budget: int, tick_steps: int = 50, digest: bool = False,
+                 keep_fields: bool = False):
         self.hbm_budget = hbm_budget
         self.tick_steps = tick_steps
         self.digest = digest
+        self.keep_fields = keep_fields
         self.batch_launches = 0
+        self.batches_built = 0
         self.peak_resident = 0
 
-    def run(self, requests, prepared=None, realtime: bool = True) -> list[Result]:
-        prepared = prepared or {r.rid: setup(r) for r in requests}
+    def run(self, requests, prepared=None, realtime: bool = True, table=None) -> list[Result]:
+        """Serve the requests; prepared: set-ups computed beforehand (not
+        counted in latency), else each request is set up after its arrival
+        from table (an eos_tables.SetupTable; built here if None)."""
+        prep = _Preparer(requests, None if prepared else _table_for(requests, table), prepared)
         pending = sorted(requests, key=lambda r: r.arrival)
         active = []            # [request, handle, steps left]
+        groups = {}            # (lattice, storage) -> (member handles, Batch)
         used, results = 0, []
         t0 = time.perf_counter()
         while pending or active:
@@ -162,7 +217,8 @@ class Server:
                 if used + need > self.hbm_budget:
                     break
                 req = pending.pop(0)
-                active.append([req, _open(req, req.storage, prepared), req.steps])
+                prep.prepare(req)
+                active.append([req, _open(req, req.storage, prep), req.steps])
                 used += need
             self.peak_resident = max(self.peak_resident, len(active))
             if not active:
@@ -170,20 +226,28 @@ class Server:
                     time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
                 continue
             k = min(self.tick_steps, min(a[2] for a in active))
-            batches = []
+            running = []
             for key in sorted({(a[0].lattice, a[0].storage) for a in active}):
                 members = [a[1] for a in active if (a[0].lattice, a[0].storage) == key]
-                b = Batch(members)
+                old = groups.get(key)
+                if old is None or old[0] != members:
+                    if old is not None:
+                        old[1].close()
+                    groups[key] = (members, Batch(members))
+                    self.batches_built += 1
+                b = groups[key][1]
+                l0 = b.launches
                 b.step(k)              # the groups' launches overlap on the GPU
-                batches.append(b)
-            for b in batches:
+                running.append((key, b, l0))
+            # host work while the GPU runs the tick: set up arrived requests
+            prep.prepare_arrived(time.perf_counter() - t0, realtime)
+            for key, b, l0 in running:
                 try:
                     b.sync()
                 except LBMError:
                     pass           # the members are checked one by one below
-                self.batch_launches += b.launches
-                b.close()
-            still = []
+                self.batch_launches += b.launches - l0
+            still, changed = [], set()
             for a in active:
                 a[2] -= k
                 try:
@@ -192,28 +256,39 @@ class Server:
                 except LBMError:
                     ok = False     # isolate a diverged solve; the others go on
                 if not ok or a[2] == 0:
-                    results.append(_finish(a[0], a[1], t0, self.digest) if ok else _failed(a[0], t0))
+                    key = (a[0].lattice, a[0].storage)
+                    if key in groups and key not in changed:
+                        groups.pop(key)[1].close()   # the members' buffers follow the batch
+                        changed.add(key)
+                    results.append(_finish(a[0], a[1], t0, self.digest, self.keep_fields)
+                                   if ok else _failed(a[0], t0))
                     a[1].close()
                     used -= footprint(a[0])
                 else:
                     still.append(a)
             active = still
+        for members, b in groups.values():
+            b.close()
         return results
 
 
-def run_sequential_f64(requests, prepared=None, realtime: bool = True) -> list[Result]:
-    """One request at a time, FP64 storage, in arrival order."""
-    prepared = prepared or {r.rid: setup(r) for r in requests}
+def run_sequential_f64(requests, prepared=None, realtime: bool = True, table=None,
+                       keep_fields: bool = False) -> list[Result]:
+    """One request at a time, FP64 storage, in arrival order; the next
+    arrived request is set up while the current one runs."""
+    prep = _Preparer(requests, None if prepared else _table_for(requests, table), prepared)
     results = []
     t0 = time.perf_counter()
     for req in sorted(requests, key=lambda r: r.arrival):
         if realtime:
             time.sleep(max(0.0, req.arrival - (time.perf_counter() - t0)))
-        g = _open(req, F64, prepared)
+        prep.prepare(req)
+        g = _open(req, F64, prep)
         g.step(req.steps)
+        prep.prepare_arrived(time.perf_counter() - t0, realtime, limit=1)
         try:
             g.sync()
-            results.append(_finish(req, g, t0))
+            results.append(_finish(req, g, t0, keep=keep_fields))
         except LBMError:
             results.append(_failed(req, t0))
         g.close()

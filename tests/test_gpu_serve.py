@@ -54,3 +54,31 @@ def test_fp64_baseline_agrees_with_reduced_precision(env):
         assert r32[rid].mass == pytest.approx(r64[rid].mass, rel=mt)
     s = serve.summarize(list(r32.values()))
     assert s["solves"] == len(reqs) and s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_served_results_against_the_oracle(env):
+    """Three requests of the mix (FP32 and FP16-shifted, D2Q9 and D3Q27)
+    served in continuous batches with the set-up done after arrival (from
+    the EOS table), their final densities compared node by node with the
+    FP64 oracle run of the same request: within 0.5 % (FP32) and 2 %
+    (FP16-shifted) of rho."""
+    from oracle.lbm import OracleLBM
+    lbm, serve, reqs, prepared = env
+    srv = serve.Server(hbm_budget=1 << 34, tick_steps=20, keep_fields=True)
+    table = serve.eos_tables.SetupTable(0, 0.6, 0.9)
+    got = {r.rid: r for r in srv.run(reqs, None, realtime=False, table=table)}
+    picked = []
+    for want in ((0, lbm.F32), (0, lbm.F16S), (1, lbm.F32), (1, lbm.F16S)):
+        picked += [r for r in reqs if (r.lattice, r.storage) == want][:1]
+    assert len(picked) >= 3
+    for req in picked:
+        prm, rho0 = serve.setup(req, table=table)
+        nz = req.n if req.lattice == 1 else 1
+        o = OracleLBM(req.lattice, req.n, req.n, nz, prm["eos"], prm["t_over_tc"], prm["kappa"],
+                      prm["tau"], a=prm["a"])
+        o.init(rho0)
+        o.step(req.steps)
+        ro = o.moments()[0]
+        tol = 5e-3 if req.storage == lbm.F32 else 2e-2
+        err = float(np.max(np.abs(got[req.rid].rho - ro) / ro))
+        assert err < tol, (req, err)

@@ -38,3 +38,19 @@ def test_set_up_tables_match_the_oracle(eos, tr):
     # the scaled attraction puts the liquid's dP/drho at (or below) 0.1
     h = 1e-6 * rl
     assert (e(rl + h) - e(rl - h)) / (2 * h) <= 0.1 + 1e-6
+
+
+def test_setup_table_matches_direct_values():
+    """The server's Chebyshev table of (a, rho_v, rho_l, kappa) over the
+    sweep's T/Tc range reproduces the direct Maxwell/width computation at
+    random T/Tc to 1e-7 relative (rho_v spans a factor of 40 there)."""
+    t = eos_tables.SetupTable(0, 0.5, 0.95)
+    rng = np.random.default_rng(3)
+    for tr in rng.uniform(0.5, 0.95, 6):
+        a = eos_tables.stable_a(0, tr)
+        rv, rl, _ = eos_tables.coexistence(0, tr, a)
+        k = eos_tables.kappa_for_width(0, tr, a)
+        got = t(tr)
+        for g, w in zip(got, (a, rv, rl, k)):
+            assert g == pytest.approx(w, rel=1e-7)
+    assert t(0.97)[2] == pytest.approx(eos_tables.coexistence(0, 0.97, eos_tables.stable_a(0, 0.97))[1])
