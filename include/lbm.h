@@ -59,7 +59,7 @@ enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q27 = 1 };
 
 /* Equations of state of Sec. 3.1: van der Waals (Eq. vdWEoS), Peng-Robinson
  * (Eq. PREoS), Redlich-Kwong-Soave (Eq. RKSEoS), Carnahan-Starling (Eq. CSEos);
- * and the two Shan-Chen forms of Appendix C, P = rho/3 + (G/6) psi_SC^2 with
+ * and the two Shan-Chen forms of Appendix G, P = rho/3 + (G/6) psi_SC^2 with
  * psi_SC = 1 - exp(-rho) (Eq. SC1, critical coupling G_c = -4) or
  * exp(-1/rho) (Eq. SC2, G_c = -e^2). For these T/Tc sets the coupling
  * G = G_c / (T/Tc), and the a, b of lbm_params are not used (b must still
@@ -112,7 +112,7 @@ typedef struct {
                             visc_rho[0], constant beyond; omega, and the
                             (1 - omega/2) of Eq. correction, per node. The
                             paper sets a vapour to liquid viscosity ratio
-                            (Sec. 6) without the interpolation. 0 (default):
+                            (Sec. 5.2) without the interpolation. 0 (default):
                             one tau everywhere. Else must exceed 1/2, and
                             0 < visc_rho[0] < visc_rho[1]. */
     double visc_rho[2];  /* rho_v, rho_l of the interpolation */
@@ -166,7 +166,16 @@ int lbm_set_stream(lbm_handle h, void *stream);
 int lbm_init(lbm_handle h, const double *rho0, const double *u0, int on_device);
 
 /* Advance n >= 0 time steps. Asynchronous on the handle's stream; steps
- * after the first are replayed from a CUDA graph of two steps. */
+ * after the first are replayed from a CUDA graph of two steps. For n > 64
+ * the device's status word is polled every 64 steps: each poll copies it to
+ * pinned host memory behind an event and first waits for the previous copy,
+ * so the call returns when at most one polling interval is still queued,
+ * and a density that became non-finite or non-positive stops the launches
+ * within 128 steps of appearing: LBM_ENONFINITE, after which the handle is
+ * in LBM_ESTATE until lbm_init or lbm_set_populations. Divergence in the
+ * last interval (or in calls with n <= 64) is reported by the next
+ * synchronising call (lbm_sync, lbm_moments, lbm_reduce). The first long
+ * call allocates the pinned word and the event (freed by lbm_destroy). */
 int lbm_step(lbm_handle h, int64_t n);
 
 /* Macroscopic fields of the current state: rho (double[N]), bare velocity
@@ -235,13 +244,15 @@ int lbm_set_chunk(lbm_handle h, int chunk);
 /* Pick the chunk of the fused FP32 step by timing candidates on the
  * handle's own state (saved to a temporary device buffer and restored
  * afterwards, so the state is unchanged). Sets and returns it in
- * *chunk_out (0 for FP64 storage, which has no tile parameter). For D3Q27
- * with LBM_F32 storage it also picks the tile height, 8 or 7 rows of 32
- * nodes (7 rows fill every SM with two CTAs in one wave where 8 rows leave
- * some SMs with one, e.g. at 128^3); the shifted storages and batches keep
- * 8 rows. Tiles and chunks change the work split only: results are
- * bitwise the same. Synchronising; allocates and frees one state-sized
- * buffer. */
+ * *chunk_out (0 for FP64 storage, which has no tile parameter). With
+ * LBM_F32 storage it also picks between the plain and the warp-specialised
+ * kernel (lbm_set_warp_specialized), and for D3Q27 the tile height, 8 or 7
+ * rows of 32 nodes (7 rows fill every SM with two CTAs in one wave where 8
+ * rows leave some SMs with one, e.g. at 128^3); the shifted storages and
+ * batches keep the plain kernel with 8 rows. Kernels, tiles and chunks
+ * change the work split only: results are bitwise the same. Synchronising;
+ * allocates and frees one state-sized buffer; on failure the handle keeps
+ * the kernel, tile and chunk it had. */
 int lbm_autotune(lbm_handle h, int *chunk_out);
 
 /* The tile of the fused step in use, in nodes: *tile_x = 32, *tile_y = 8 or
@@ -255,6 +266,21 @@ int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y);
  * the speed change. LBM_EINVAL for another height, another lattice or
  * storage. */
 int lbm_set_tile(lbm_handle h, int tile_y);
+
+/* Select the warp-specialised form of the LBM_F32 fused step (on != 0) or
+ * the plain one (0, the default). The warp-specialised kernel runs two
+ * thread groups per tile: one forms each entering plane's densities,
+ * pseudo-potentials and velocities (the first half of the step), the other
+ * collides and streams the plane two behind it, and the groups hand planes
+ * over through shared-memory barriers instead of a barrier of the whole
+ * block per plane. Same arithmetic in the same order: results are bitwise
+ * those of the plain kernel. A wait between the groups that does not end
+ * within about a second (a fault, never normal operation) makes the next
+ * synchronising call return LBM_ETIMEOUT. LBM_EINVAL for other storage. */
+int lbm_set_warp_specialized(lbm_handle h, int on);
+
+/* *on = 1 if the warp-specialised LBM_F32 step is selected, else 0. */
+int lbm_get_warp_specialized(lbm_handle h, int *on);
 
 /* ---- Batches: many lattices advanced by one persistent launch ----------
  * A batch holds count >= 1 distinct, initialised handles with the same

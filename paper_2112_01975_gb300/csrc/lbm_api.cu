@@ -29,6 +29,7 @@ struct lbm_ctx {
     GeoF geof;     // FP32 fused step: 3D frame (D2Q9: ny = 1, nz = 2D y extent)
     PhysF physf;
     int tile_rows = 8;   // D3Q27 FP32 step: 32 x 8 (lbmf) or 32 x 7 (lbmf7) tiles
+    bool ws = false;     // FP32 step: warp-specialised kernel (k_step_f32_ws)
     int storage, flags;
     double t_over_tc, tau;
     std::vector<uint8_t> mask_host;
@@ -49,6 +50,11 @@ struct lbm_ctx {
     bool initialised = false, bad = false;
     cudaGraphExec_t graph = nullptr;
     int64_t launches = 0;
+    // status polling of long lbm_step calls: a pinned copy of the status word
+    // and the event that marks its arrival
+    int *poll_host = nullptr;
+    cudaEvent_t poll_ev = nullptr;
+    bool poll_pending = false;
     // interpolated bounce-back: boundary nodes, their active links, wall distances
     int nb = 0;
     unsigned *bn = nullptr, *bmask = nullptr;
@@ -148,7 +154,7 @@ double eos_rtc(int eos, double a, double b)
     case LBM_EOS_PR: return (0.0778 / 0.45724) * a / b;
     case LBM_EOS_RKS: return (0.08664 / 0.42748) * a / b;
     case LBM_EOS_CS: return (0.18727 / 0.4963) * a / b;
-    case LBM_EOS_SC1: return -4.0;          // critical coupling G_c (Appendix C)
+    case LBM_EOS_SC1: return -4.0;          // critical coupling G_c (Appendix G)
     case LBM_EOS_SC2: return -std::exp(2.0);
     }
     return NAN;
@@ -245,13 +251,33 @@ T as_layout(const U &u)
 template <bool MASK>
 void launch_fused_r7(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
-    static std::atomic<unsigned long long> done{0};   // devices already opted in
     using L = lbmf7::LatF<1>;
+    if (h->ws) {
+        static std::atomic<unsigned long long> done{0};   // devices already opted in
+        const int bytes = (int)sizeof(lbmf7::SharedWS<1>);
+        smem_opt_in(lbmf7::k_step_f32_ws<1, MASK>, bytes, done);
+        lbmf7::k_step_f32_ws<1, MASK><<<fused_grid<1>(h->geof, L::TY), 2 * L::TX * L::TY, bytes, s>>>(
+            as_layout<lbmf7::GeoF>(h->geof), as_layout<lbmf7::PhysF>(h->physf), h->mask, src, dst,
+            h->status);
+        return;
+    }
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
     const int bytes = (int)sizeof(lbmf7::SharedF<1>);
     smem_opt_in(lbmf7::k_step_f32<1, MASK>, bytes, done);
     lbmf7::k_step_f32<1, MASK><<<fused_grid<1>(h->geof, L::TY), L::TX * L::TY, bytes, s>>>(
         as_layout<lbmf7::GeoF>(h->geof), as_layout<lbmf7::PhysF>(h->physf), h->mask, src, dst,
         h->status);
+}
+
+template <int LAT, bool MASK>
+void launch_fused_ws(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    using L = lbmf::LatF<LAT>;
+    const int bytes = (int)sizeof(lbmf::SharedWS<LAT>);
+    smem_opt_in(lbmf::k_step_f32_ws<LAT, MASK>, bytes, done);
+    lbmf::k_step_f32_ws<LAT, MASK><<<fused_grid<LAT>(h->geof), 2 * L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, src, dst, h->status);
 }
 
 template <int LAT>
@@ -260,6 +286,11 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
     if (LAT == 1 && h->tile_rows == 7) {
         if (has_solid(h)) launch_fused_r7<true>(h, s, src, dst);
         else              launch_fused_r7<false>(h, s, src, dst);
+        return;
+    }
+    if (h->ws) {
+        if (has_solid(h)) launch_fused_ws<LAT, true>(h, s, src, dst);
+        else              launch_fused_ws<LAT, false>(h, s, src, dst);
         return;
     }
     static std::atomic<unsigned long long> done_m{0}, done_f{0};   // devices already opted in
@@ -426,6 +457,8 @@ int read_status(lbm_ctx *h)
     CU(h, cudaStreamSynchronize(h->stream));
     if (st) {
         h->bad = true;
+        if (st & 2)
+            return fail(h, LBM_ETIMEOUT, "a wait between the fused step's thread groups timed out");
         return fail(h, LBM_ENONFINITE, "a density became non-finite or non-positive");
     }
     return LBM_OK;
@@ -560,6 +593,39 @@ int launch_reduce(lbm_ctx *h)
     lbmk::k_reduce_final<<<1, lbmk::RED_BLOCKS, 0, h->stream>>>(h->partial, h->sums);
     CU(h, cudaGetLastError());
     h->launches += 2;
+    return LBM_OK;
+}
+
+// Status polling of long step sequences: every kPollReplays graph replays
+// (2 steps each) the status word is copied to pinned host memory behind an
+// event; before the next copy is queued the previous one is awaited, so the
+// host runs at most one polling interval ahead of the device and a diverged
+// lattice stops within two intervals.
+constexpr int64_t kPollReplays = 32;
+
+int ensure_poll(lbm_ctx *h)
+{
+    if (h->poll_host) return LBM_OK;
+    CU(h, cudaHostAlloc(reinterpret_cast<void **>(&h->poll_host), sizeof(int), cudaHostAllocDefault));
+    *h->poll_host = 0;
+    CU(h, cudaEventCreateWithFlags(&h->poll_ev, cudaEventDisableTiming));
+    return LBM_OK;
+}
+
+// Wait for the last queued status copy and act on it; queue the next one.
+int poll_status(lbm_ctx *h)
+{
+    if (h->poll_pending) {
+        CU(h, cudaEventSynchronize(h->poll_ev));
+        h->poll_pending = false;
+        if (*h->poll_host) {
+            h->bad = true;
+            return fail(h, LBM_ENONFINITE, "a density became non-finite or non-positive");
+        }
+    }
+    CU(h, cudaMemcpyAsync(h->poll_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaEventRecord(h->poll_ev, h->stream));
+    h->poll_pending = true;
     return LBM_OK;
 }
 
@@ -776,7 +842,11 @@ int lbm_step(lbm_handle h, int64_t n)
             --n;
         }
         if ((rc = ensure_graph(h))) return rc;
-        for (int64_t k = 0; k < n / 2; ++k) {
+        const int64_t reps = n / 2;
+        if (reps > kPollReplays && (rc = ensure_poll(h))) return rc;
+        h->poll_pending = false;
+        for (int64_t k = 0; k < reps; ++k) {
+            if (k > 0 && k % kPollReplays == 0 && (rc = poll_status(h))) return rc;
             CU(h, cudaGraphLaunch(h->graph, h->stream));
             h->launches += 2 * kernels_per_step(h);
         }
@@ -1304,25 +1374,41 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
                               cudaMemcpyDeviceToDevice, h->stream));
     const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128};
     const int nz = h->geof.nz;
-    // D3Q27 FP32: 32 x 8 and 32 x 7 tiles (the shifted and batched steps use 32 x 8)
-    const bool two_heights = h->lattice == LBM_D3Q27 && h->storage == LBM_F32;
+    const int chunk0 = h->geof.chunk, rows0 = h->tile_rows;   // restored on failure
+    // FP32: the plain and the warp-specialised kernel; D3Q27 FP32 also 32 x 8
+    // and 32 x 7 tiles (the shifted and batched steps use plain 32 x 8)
+    const bool fp32 = h->storage == LBM_F32;
+    const bool two_heights = h->lattice == LBM_D3Q27 && fp32;
+    const bool ws0 = h->ws;
     int best = h->geof.chunk, best_rows = h->tile_rows;
+    bool best_ws = h->ws;
     double best_ms = 1e30;
-    for (int rows : {8, 7}) {
-        if (rows == 7 && !two_heights) continue;
-        h->tile_rows = rows;
-        for (int c : cands) {
-            if (c > nz && c != cands[0]) continue;
-            h->geof.chunk = c;
-            double ms[2];
-            rc = lbm_time_kernels(h, 1, ms);                  // warm-up
-            if (rc == LBM_OK) rc = lbm_time_kernels(h, 6, ms);
+    for (int spec = 0; spec < (fp32 ? 2 : 1) && rc == LBM_OK; ++spec) {
+        h->ws = spec == 1;
+        for (int rows : {8, 7}) {
+            if (rows == 7 && !two_heights) continue;
+            h->tile_rows = rows;
+            for (int c : cands) {
+                if (c > nz && c != cands[0]) continue;
+                h->geof.chunk = c;
+                double ms[2];
+                rc = lbm_time_kernels(h, 1, ms);                  // warm-up
+                if (rc == LBM_OK) rc = lbm_time_kernels(h, 6, ms);
+                if (rc != LBM_OK) break;
+                if (ms[1] < best_ms) { best_ms = ms[1]; best = c; best_rows = rows; best_ws = h->ws; }
+            }
             if (rc != LBM_OK) break;
-            if (ms[1] < best_ms) { best_ms = ms[1]; best = c; best_rows = rows; }
         }
-        if (rc != LBM_OK) break;
     }
-    h->tile_rows = best_rows;
+    // the best candidate, or on failure the kernel, chunk and tile the handle
+    // had; a graph captured before the search may hold either, so it is dropped
+    h->tile_rows = rc == LBM_OK ? best_rows : rows0;
+    h->geof.chunk = rc == LBM_OK ? best : chunk0;
+    h->ws = rc == LBM_OK ? best_ws : ws0;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     cudaError_t e = cudaMemcpyAsync(h->fv[0], save, bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess && rbytes)
         e = cudaMemcpyAsync(h->rs[0], static_cast<char *>(save) + bytes, rbytes,
@@ -1332,15 +1418,6 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
     h->cur = 0;
     if (rc != LBM_OK) return rc;
-    if (h->graph && h->geof.chunk != best) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
-    }
-    h->geof.chunk = best;
-    if (h->graph) {   // the captured graph may have been made with another chunk
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
-    }
     if (chunk_out) *chunk_out = best;
     return LBM_OK;
 }
@@ -1373,6 +1450,26 @@ int lbm_set_tile(lbm_handle h, int tile_y)
     return LBM_OK;
 }
 
+int lbm_set_warp_specialized(lbm_handle h, int on)
+{
+    if (!h) return LBM_EINVAL;
+    if (h->storage != LBM_F32)
+        return fail(h, LBM_EINVAL, "the warp-specialised kernel is a form of the FP32 step only");
+    if (h->ws != (on != 0) && h->graph) {   // the captured graph holds the other kernel
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->ws = on != 0;
+    return LBM_OK;
+}
+
+int lbm_get_warp_specialized(lbm_handle h, int *on)
+{
+    if (!h || !on) return LBM_EINVAL;
+    *on = h->ws ? 1 : 0;
+    return LBM_OK;
+}
+
 int lbm_set_chunk(lbm_handle h, int chunk)
 {
     if (!h) return LBM_EINVAL;
@@ -1398,6 +1495,8 @@ void lbm_destroy(lbm_handle h)
     if (h->bmask) cudaFree(h->bmask);
     if (h->bq) cudaFree(h->bq);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    if (h->poll_ev) cudaEventDestroy(h->poll_ev);
+    if (h->poll_host) cudaFreeHost(h->poll_host);
     cudaGetLastError();
     delete h;
 }

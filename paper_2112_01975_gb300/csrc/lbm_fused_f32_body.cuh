@@ -93,7 +93,7 @@ template <int LAT> __device__ __forceinline__ constexpr float weight_f(int i)
            (L::cz(i) ? 1.0f / 6.0f : 2.0f / 3.0f);
 }
 
-// P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 and Appendix C equations of state).
+// P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 and Appendix G equations of state).
 // Every operation is an explicitly rounded intrinsic, so each inlined call
 // site rounds the same way (no call-site-dependent contraction).
 __device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
@@ -176,30 +176,67 @@ __device__ __forceinline__ float decode_pop(ST hv, int i, int r, int c, int q, c
 // Source densities of one plane (ring index q) on the 3-halo into the ring.
 template <int LAT, typename SM>
 __device__ __forceinline__ void load_rho_plane(SM &sm, const GeoF &g, const float *__restrict__ rho_src,
-                                               int z0, int q)
+                                               int z0, int q, int t, int nt)
 {
     constexpr int RX = SM::RX, RY = SM::RY, QS = SM::QS;
-    constexpr int NT = LatF<LAT>::TX * LatF<LAT>::TY;
     const int zq = ((z0 - 2 + q) % g.nz + g.nz) % g.nz;
     const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
-    for (int k = threadIdx.x; k < RX * RY; k += NT) {
+    for (int k = t; k < RX * RY; k += nt) {
         const int r = k / RX, c = k - r * RX;
         sm.rs[(q + QS) & (QS - 1)][r][c] =
             __ldg(rho_src + ((unsigned)sm.rxw[c] + (unsigned)g.nx * (unsigned)sm.ryw[r] + plane * (unsigned)zq));
     }
 }
 
-// One CTA's work: the column tile (bx, by) over the plane chunk bz.
-template <int LAT, bool MASK, typename ST = float, typename SM = SharedF<LAT>>
-__device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
-                                           const uint8_t *__restrict__ mask,
-                                           const ST *__restrict__ f, ST *__restrict__ fout,
-                                           int *__restrict__ status, int bx, int by, int bz,
-                                           SM &sm, const float *__restrict__ rho_src = nullptr,
-                                           float *__restrict__ rho_dst = nullptr)
+// Per-tile constants of one CTA's work: the column tile at (x0, y0) over the
+// planes z0 .. z1-1; planes z0-2 .. z1+1 enter the rings one per iteration,
+// plane z0-2+pl with ring index pl, np iterations.
+struct TileF {
+    int x0, y0, z0, z1, np;
+};
+
+// Wrapped halo coordinates of the tile (bx, by, bz) and, for shifted
+// storage, the source densities of its first planes; threads t = 0..nt-1 of
+// the CTA share the work. The caller synchronises before the rings are used.
+template <int LAT, typename ST, typename SM>
+__device__ __forceinline__ TileF tile_setup(const GeoF &g, int bx, int by, int bz, SM &sm, int t,
+                                            int nt, const float *__restrict__ rho_src)
+{
+    using L = LatF<LAT>;
+    constexpr bool THREE = LAT == 1;
+    constexpr int AX = SharedF<LAT>::AX, AY = SharedF<LAT>::AY, HY = L::HY;
+    TileF T;
+    T.x0 = bx * L::TX;
+    T.y0 = by * L::TY;
+    T.z0 = bz * g.chunk;
+    T.z1 = min(T.z0 + g.chunk, g.nz);
+    T.np = (T.z1 - T.z0) + 4;
+    for (int c = t; c < AX; c += nt) sm.xw[c] = ((T.x0 - 2 + c) % g.nx + g.nx) % g.nx;
+    for (int r = t; r < AY; r += nt) sm.yw[r] = THREE ? ((T.y0 - HY + r) % g.ny + g.ny) % g.ny : 0;
+    if constexpr (IsShifted<ST>::value) {
+        for (int c = t; c < SM::RX; c += nt) sm.rxw[c] = ((T.x0 - 3 + c) % g.nx + g.nx) % g.nx;
+        for (int r = t; r < SM::RY; r += nt)
+            sm.ryw[r] = THREE ? ((T.y0 - HY - 1 + r) % g.ny + g.ny) % g.ny : 0;
+        __syncthreads();
+        load_rho_plane<LAT>(sm, g, rho_src, T.z0, -1, t, nt);
+        load_rho_plane<LAT>(sm, g, rho_src, T.z0, 0, t, nt);
+        load_rho_plane<LAT>(sm, g, rho_src, T.z0, 1, t, nt);
+    }
+    return T;
+}
+
+// Phase A of iteration pl: plane z0 - 2 + pl enters the rings (ring index
+// pl): (rho, |psi|) on the 2-node halo, rho u_a^3 on the 1-node halo, the sign
+// of P - P0 and (u, 1/rho) of the interior nodes; thread tid of NT. Each
+// thread owns up to KA halo nodes and issues all their loads before any
+// arithmetic, for memory-level parallelism.
+template <int LAT, bool MASK, typename ST, typename SM>
+__device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
+                                        const uint8_t *__restrict__ mask,
+                                        const ST *__restrict__ f, SM &sm, const TileF &T,
+                                        int pl, int tid, const float *__restrict__ rho_src)
 {
     constexpr bool SHIFT = IsShifted<ST>::value;
-    static_assert(!(SHIFT && MASK), "shifted storage runs lattices without solid nodes");
     using L = LatF<LAT>;
     constexpr int Q = L::Q, TX = L::TX, TY = L::TY, HY = L::HY;
     constexpr bool THREE = LAT == 1;
@@ -211,245 +248,373 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
     auto &s_g = sm.g;
     auto &s_xw = sm.xw;
     auto &s_yw = sm.yw;
-
-    const int tid = threadIdx.x;
-    const int x0 = bx * TX, y0 = by * TY;
-    const int z0 = bz * g.chunk;
-    const int z1 = min(z0 + g.chunk, g.nz);
-    const int tx = tid % TX, ty = tid / TX;
-    const int xi = x0 + tx, yi = y0 + ty;
-    const bool inside = xi < g.nx && yi < g.ny;
+    const int z0 = T.z0;
     const unsigned N = g.N;
     const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
-    for (int c = tid; c < AX; c += NT) s_xw[c] = ((x0 - 2 + c) % g.nx + g.nx) % g.nx;
-    for (int r = tid; r < AY; r += NT) s_yw[r] = THREE ? ((y0 - HY + r) % g.ny + g.ny) % g.ny : 0;
-    if constexpr (SHIFT) {
-        for (int c = tid; c < SM::RX; c += NT) sm.rxw[c] = ((x0 - 3 + c) % g.nx + g.nx) % g.nx;
-        for (int r = tid; r < SM::RY; r += NT)
-            sm.ryw[r] = THREE ? ((y0 - HY - 1 + r) % g.ny + g.ny) % g.ny : 0;
-        __syncthreads();
-        load_rho_plane<LAT>(sm, g, rho_src, z0, -1);
-        load_rho_plane<LAT>(sm, g, rho_src, z0, 0);
-        load_rho_plane<LAT>(sm, g, rho_src, z0, 1);
-    }
-    __syncthreads();
-
-    // Planes z0-2 .. z1+1 enter the rings one per iteration; plane z0-2+pl
-    // has ring index pl. Six (rho, |psi|) slots and five rho u^3 slots let
-    // the next plane enter while slower warps still collide: one barrier
-    // per plane.
-    const int np = (z1 - z0) + 4;
-    for (int pl = 0; pl < np; ++pl) {
-        // ---- phase A: plane z0 - 2 + pl enters the rings -------------------
-        // Each thread owns up to KA halo nodes and issues all their loads
-        // before any arithmetic, for memory-level parallelism.
-        {
-            constexpr int KA = (AX * AY + NT - 1) / NT;
-            const int zl = wrapf(z0 - 2 + pl, g.nz);
-            const int rs = pl % RS, gs = pl % GS;
-            float fi[KA][Q];
-            unsigned nk[KA];
-            bool live[KA], solid[KA];
-            if constexpr (SHIFT) load_rho_plane<LAT>(sm, g, rho_src, z0, pl + 2);   // for the next iteration
+    constexpr int KA = (AX * AY + NT - 1) / NT;
+    const int zl = wrapf(z0 - 2 + pl, g.nz);
+    const int rs = pl % RS, gs = pl % GS;
+    float fi[KA][Q];
+    unsigned nk[KA];
+    bool live[KA], solid[KA];
+    if constexpr (SHIFT) load_rho_plane<LAT>(sm, g, rho_src, z0, pl + 2, tid, NT);   // for the next iteration
 #pragma unroll
-            for (int u = 0; u < KA; ++u) {
-                const int k = tid + u * NT;
-                live[u] = k < AX * AY;
-                const int kk = live[u] ? k : 0;
-                const int r = kk / AX, c = kk - r * AX;
-                nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
-                solid[u] = MASK && live[u] && mask[nk[u]];
-                if (live[u] && !solid[u]) {
+    for (int u = 0; u < KA; ++u) {
+        const int k = tid + u * NT;
+        live[u] = k < AX * AY;
+        const int kk = live[u] ? k : 0;
+        const int r = kk / AX, c = kk - r * AX;
+        nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
+        solid[u] = MASK && live[u] && mask[nk[u]];
+        if (live[u] && !solid[u]) {
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < KA; ++u) {
-                if (!live[u]) continue;
-                const int k = tid + u * NT;
-                const int r = k / AX, c = k - r * AX;
-                const bool ring1 = c >= 1 && c < AX - 1 && (!THREE || (r >= 1 && r < AY - 1));
-                float rho, d, gx = 0.0f, gy = 0.0f, gz = 0.0f;
-                float4 uvk = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (solid[u]) {
-                    rho = p.rho_w;
-                    d = p.spsi_w;
-                } else {
-                    // x-row sums for each (cy, cz), then the moments from them
-                    constexpr int R = Q / 3;
-                    float row[R], jx = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        row[q] = fi[u][3 * q] + fi[u][3 * q + 1] + fi[u][3 * q + 2];
-                        jx += fi[u][3 * q + 2] - fi[u][3 * q];
-                    }
-                    rho = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < R; ++q) rho += row[q];
-                    if (ring1) {
-                        float jy = 0.0f, jz = 0.0f;
-#pragma unroll
-                        for (int q = 0; q < R; ++q) {
-                            const int cy = THREE ? q % 3 - 1 : 0, cz = THREE ? q / 3 - 1 : q - 1;
-                            if (cy > 0) jy += row[q];
-                            if (cy < 0) jy -= row[q];
-                            if (cz > 0) jz += row[q];
-                            if (cz < 0) jz -= row[q];
-                        }
-                        const float inv = __frcp_rn(rho);
-                        const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-                        gx = rho * ux * ux * ux;
-                        gy = rho * uy * uy * uy;
-                        gz = rho * uz * uz * uz;
-                        uvk = make_float4(ux, uy, uz, inv);
-                    }
-                    d = excess_pressure_f(p, rho);
-                }
-                s_rp[rs][r][c] = f2(rho, sqrtf(fabsf(d)));
-                if (ring1) {
-                    const int gr = THREE ? r - 1 : 0;
-                    s_g[gs][0][gr][c - 1] = gx;
-                    s_g[gs][1][gr][c - 1] = gy;
-                    s_g[gs][2][gr][c - 1] = gz;
-                }
-                const int ir = r - HY, ic = c - 2;
-                if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) {
-                    s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
-                    sm.uv[pl & 3][ir][ic] = uvk;
-                }
-            }
+            for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
         }
-        __syncthreads();
-        // ---- phase B: collide plane zc = z0 + pl - 4 --------------------------
-        if (pl >= 4 && inside) {
-            const int pc = pl - 2;             // ring index of the collided plane
-            const int zc = z0 + pl - 4;
-            const unsigned n = (unsigned)xi + (unsigned)g.nx * (unsigned)yi + plane * (unsigned)zc;
-            if (!(MASK && mask[n])) {
-                // the node's own populations (second read, an L2 hit), issued first
-                float fi[Q];
+    }
 #pragma unroll
-                for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
-                const int cr = ty + HY, cc = tx + 2;
-                const float2 c0 = s_rp[pc % RS][cr][cc];
-                const float rho = c0.x;
-                const float spsi = s_sg[pc % RS][ty][tx] * c0.y;
-                if (!(rho > 0.0f) || !isfinite(rho)) atomicOr(status, 1);
-                if constexpr (SHIFT) rho_dst[n] = rho;   // source density of what this node pushes
-                // Korteweg force (Eq. Kforce_final, sign as the force on the fluid).
-                // Per ring s, the pairs (|psi|, rho) of neighbours with c_a = +1 and
-                // c_a = -1 are summed by weight class (centre, edge, corner).
-                int slot[5];
+    for (int u = 0; u < KA; ++u) {
+        if (!live[u]) continue;
+        const int k = tid + u * NT;
+        const int r = k / AX, c = k - r * AX;
+        const bool ring1 = c >= 1 && c < AX - 1 && (!THREE || (r >= 1 && r < AY - 1));
+        float rho, d, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+        float4 uvk = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (solid[u]) {
+            rho = p.rho_w;
+            d = p.spsi_w;
+        } else {
+            // x-row sums for each (cy, cz), then the moments from them
+            constexpr int R = Q / 3;
+            float row[R], jx = 0.0f;
 #pragma unroll
-                for (int dz = 0; dz < 5; ++dz) slot[dz] = (pc - 2 + dz) % RS;
-                float2 S[3] = {f2(0.0f, 0.0f), f2(0.0f, 0.0f), f2(0.0f, 0.0f)};   // (S_psi, S_rho)
-                const float2 neg1 = f2(-1.0f, -1.0f);
+            for (int q = 0; q < R; ++q) {
+                row[q] = fi[u][3 * q] + fi[u][3 * q + 1] + fi[u][3 * q + 2];
+                jx += fi[u][3 * q + 2] - fi[u][3 * q];
+            }
+            rho = 0.0f;
 #pragma unroll
-                for (int s = 1; s <= 2; ++s) {
-                    float2 P[3][3], M[3][3];
+            for (int q = 0; q < R; ++q) rho += row[q];
+            if (ring1) {
+                float jy = 0.0f, jz = 0.0f;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) { P[a][k] = f2(0.0f, 0.0f); M[a][k] = f2(0.0f, 0.0f); }
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
-                        if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
-                        const float2 r2 = s_rp[slot[2 + s * c[2]]][cr + s * c[1]][cc + s * c[0]];
-                        const float2 v = f2(r2.y, r2.x);   // (|psi|, rho)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            if (c[a] == 0) continue;
-                            const int k = (a != 0 && c[0] != 0) + (a != 1 && c[1] != 0) +
-                                          (a != 2 && c[2] != 0);
-                            if (c[a] > 0) P[a][k] = __fadd2_rn(P[a][k], v);
-                            else          M[a][k] = __fadd2_rn(M[a][k], v);
-                        }
-                    }
-                    // weights w_i/cs2 c_a = 1/2 W(c_b) W(c_c): D3Q27 2/9, 1/18, 1/72;
-                    // D2Q9 1/3, 1/12; ring coefficients (4/3, 2) and (-1/6, -1)
-                    const float2 gsr = s == 1 ? f2(4.0f / 3.0f, 2.0f) : f2(-1.0f / 6.0f, -1.0f);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        if (!THREE && a == 1) continue;
-                        const float2 D0 = __ffma2_rn(M[a][0], neg1, P[a][0]);
-                        const float2 D1 = __ffma2_rn(M[a][1], neg1, P[a][1]);
-                        float2 Dw;
-                        if (THREE) {
-                            const float2 D2 = __ffma2_rn(M[a][2], neg1, P[a][2]);
-                            Dw = __fmul2_rn(D0, f2(2.0f / 9.0f, 2.0f / 9.0f));
-                            Dw = __ffma2_rn(D1, f2(1.0f / 18.0f, 1.0f / 18.0f), Dw);
-                            Dw = __ffma2_rn(D2, f2(1.0f / 72.0f, 1.0f / 72.0f), Dw);
-                        } else {
-                            Dw = __fmul2_rn(D0, f2(1.0f / 3.0f, 1.0f / 3.0f));
-                            Dw = __ffma2_rn(D1, f2(1.0f / 12.0f, 1.0f / 12.0f), Dw);
-                        }
-                        S[a] = __ffma2_rn(Dw, gsr, S[a]);
-                    }
+                for (int q = 0; q < R; ++q) {
+                    const int cy = THREE ? q % 3 - 1 : 0, cz = THREE ? q / 3 - 1 : q - 1;
+                    if (cy > 0) jy += row[q];
+                    if (cy < 0) jy -= row[q];
+                    if (cz > 0) jz += row[q];
+                    if (cz < 0) jz -= row[q];
                 }
-                float F[3];
+                const float inv = __frcp_rn(rho);
+                const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+                gx = rho * ux * ux * ux;
+                gy = rho * uy * uy * uy;
+                gz = rho * uz * uz * uz;
+                uvk = make_float4(ux, uy, uz, inv);
+            }
+            d = excess_pressure_f(p, rho);
+        }
+        s_rp[rs][r][c] = f2(rho, sqrtf(fabsf(d)));
+        if (ring1) {
+            const int gr = THREE ? r - 1 : 0;
+            s_g[gs][0][gr][c - 1] = gx;
+            s_g[gs][1][gr][c - 1] = gy;
+            s_g[gs][2][gr][c - 1] = gz;
+        }
+        const int ir = r - HY, ic = c - 2;
+        if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) {
+            s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
+            sm.uv[pl & 3][ir][ic] = uvk;
+        }
+    }
+}
+
+// Phase B of iteration pl >= 4: the tile's nodes on plane zc = z0 + pl - 4
+// (ring index pl - 2) collide with all stencil reads from the rings and push
+// their post-collision populations with halfway bounce-back; thread tid of
+// NT owns node (tid % TX, tid / TX), which the caller has checked to lie in
+// the lattice (a ragged tile's last columns or rows may not).
+template <int LAT, bool MASK, typename ST, typename SM>
+__device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
+                                        const uint8_t *__restrict__ mask,
+                                        const ST *__restrict__ f, ST *__restrict__ fout,
+                                        int *__restrict__ status, SM &sm, const TileF &T, int pl,
+                                        int tid, float *__restrict__ rho_dst)
+{
+    constexpr bool SHIFT = IsShifted<ST>::value;
+    using L = LatF<LAT>;
+    constexpr int Q = L::Q, TX = L::TX, HY = L::HY;
+    constexpr bool THREE = LAT == 1;
+    constexpr int RS = SharedF<LAT>::RS, GS = SharedF<LAT>::GS;
+    auto &s_rp = sm.rp;
+    auto &s_sg = sm.sg;
+    auto &s_g = sm.g;
+    const int z0 = T.z0;
+    const int tx = tid % TX, ty = tid / TX;
+    const int xi = T.x0 + tx, yi = T.y0 + ty;
+    const unsigned N = g.N;
+    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
+    const int pc = pl - 2;             // ring index of the collided plane
+    const int zc = z0 + pl - 4;
+    const unsigned n = (unsigned)xi + (unsigned)g.nx * (unsigned)yi + plane * (unsigned)zc;
+    if (!(MASK && mask[n])) {
+        // the node's own populations (second read, an L2 hit), issued first
+        float fi[Q];
 #pragma unroll
-                for (int a = 0; a < 3; ++a)   // Korteweg force plus the body force rho g
-                    F[a] = __fmaf_rn(rho, p.g[a], -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y);
-                // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2, the node's omega
-                const float om = p.var_visc ? omega_var_f(p, rho) : p.omega;
-                const float pref = p.var_visc ? p.phi_sign * (1.0f - 0.5f * om) : p.phi_pref;
-                const float omw = p.var_visc ? 1.0f - om : p.omw;
-                const int gr0 = THREE ? ty + 1 : 0, gc0 = tx + 1;
-                float Phi[3];
-                Phi[0] = pref * 0.5f * (s_g[pc % GS][0][gr0][gc0 + 1] - s_g[pc % GS][0][gr0][gc0 - 1]);
-                Phi[1] = THREE ? pref * 0.5f *
-                                     (s_g[pc % GS][1][gr0 + 1][gc0] - s_g[pc % GS][1][gr0 - 1][gc0])
-                               : 0.0f;
-                Phi[2] = pref * 0.5f *
-                         (s_g[(pc + 1) % GS][2][gr0][gc0] - s_g[(pc - 1) % GS][2][gr0][gc0]);
-                // bare velocity and 1/rho of the node, formed by phase A from the same populations
-                const float4 uvn = sm.uv[pc & 3][ty][tx];
-                const float inv = uvn.w;
-                const float un[3] = {uvn.x, uvn.y, uvn.z};
-                // product-form factors, paired (equilibrium, extended)
-                float2 ES[3][3];
+        for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
+        const int cr = ty + HY, cc = tx + 2;
+        const float2 c0 = s_rp[pc % RS][cr][cc];
+        const float rho = c0.x;
+        const float spsi = s_sg[pc % RS][ty][tx] * c0.y;
+        if (!(rho > 0.0f) || !isfinite(rho)) atomicOr(status, 1);
+        if constexpr (SHIFT) rho_dst[n] = rho;   // source density of what this node pushes
+        // Korteweg force (Eq. Kforce_final, sign as the force on the fluid).
+        // Per ring s, the pairs (|psi|, rho) of neighbours with c_a = +1 and
+        // c_a = -1 are summed by weight class (centre, edge, corner).
+        int slot[5];
+#pragma unroll
+        for (int dz = 0; dz < 5; ++dz) slot[dz] = (pc - 2 + dz) % RS;
+        float2 S[3] = {f2(0.0f, 0.0f), f2(0.0f, 0.0f), f2(0.0f, 0.0f)};   // (S_psi, S_rho)
+        const float2 neg1 = f2(-1.0f, -1.0f);
+#pragma unroll
+        for (int s = 1; s <= 2; ++s) {
+            float2 P[3][3], M[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { P[a][k] = f2(0.0f, 0.0f); M[a][k] = f2(0.0f, 0.0f); }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+                if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
+                const float2 r2 = s_rp[slot[2 + s * c[2]]][cr + s * c[1]][cc + s * c[0]];
+                const float2 v = f2(r2.y, r2.x);   // (|psi|, rho)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    if (!THREE && a == 1) {
-                        ES[1][0] = ES[1][1] = ES[1][2] = f2(1.0f, 1.0f);
-                        continue;
-                    }
-                    const float ua = un[a];
-                    const float ze = 1.0f / 3.0f + ua * ua;
-                    const float xs = ua + F[a] * inv;
-                    const float zs = 1.0f / 3.0f + xs * xs + Phi[a] * inv;
-                    ES[a][0] = f2(0.5f * (ze - ua), 0.5f * (zs - xs));
-                    ES[a][1] = f2(1.0f - ze, 1.0f - zs);
-                    ES[a][2] = f2(0.5f * (ze + ua), 0.5f * (zs + xs));
+                    if (c[a] == 0) continue;
+                    const int k = (a != 0 && c[0] != 0) + (a != 1 && c[1] != 0) +
+                                  (a != 2 && c[2] != 0);
+                    if (c[a] > 0) P[a][k] = __fadd2_rn(P[a][k], v);
+                    else          M[a][k] = __fadd2_rn(M[a][k], v);
                 }
-                float2 A[3][3];
-                const float2 rr = f2(rho, rho);
+            }
+            // weights w_i/cs2 c_a = 1/2 W(c_b) W(c_c): D3Q27 2/9, 1/18, 1/72;
+            // D2Q9 1/3, 1/12; ring coefficients (4/3, 2) and (-1/6, -1)
+            const float2 gsr = s == 1 ? f2(4.0f / 3.0f, 2.0f) : f2(-1.0f / 6.0f, -1.0f);
 #pragma unroll
-                for (int cx = 0; cx < 3; ++cx) {
-                    const float2 rx = __fmul2_rn(rr, ES[0][cx]);
-#pragma unroll
-                    for (int cy = 0; cy < 3; ++cy) A[cx][cy] = __fmul2_rn(rx, ES[1][cy]);
+            for (int a = 0; a < 3; ++a) {
+                if (!THREE && a == 1) continue;
+                const float2 D0 = __ffma2_rn(M[a][0], neg1, P[a][0]);
+                const float2 D1 = __ffma2_rn(M[a][1], neg1, P[a][1]);
+                float2 Dw;
+                if (THREE) {
+                    const float2 D2 = __ffma2_rn(M[a][2], neg1, P[a][2]);
+                    Dw = __fmul2_rn(D0, f2(2.0f / 9.0f, 2.0f / 9.0f));
+                    Dw = __ffma2_rn(D1, f2(1.0f / 18.0f, 1.0f / 18.0f), Dw);
+                    Dw = __ffma2_rn(D2, f2(1.0f / 72.0f, 1.0f / 72.0f), Dw);
+                } else {
+                    Dw = __fmul2_rn(D0, f2(1.0f / 3.0f, 1.0f / 3.0f));
+                    Dw = __ffma2_rn(D1, f2(1.0f / 12.0f, 1.0f / 12.0f), Dw);
                 }
-                // post = f* + (1 - omega)(f - feq), pushed to r + c_i
-                const int X[3] = {wrapf(xi - 1, g.nx), xi, wrapf(xi + 1, g.nx)};
-                const int Y[3] = {THREE ? wrapf(yi - 1, g.ny) : 0, yi, THREE ? wrapf(yi + 1, g.ny) : 0};
-                const int Z[3] = {wrapf(zc - 1, g.nz), zc, wrapf(zc + 1, g.nz)};
+                S[a] = __ffma2_rn(Dw, gsr, S[a]);
+            }
+        }
+        float F[3];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-                    const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
-                    const float post = SHIFT ? fmaf(fmaf(omw, fi[i] - es.x, es.y), inv, -weight_f<LAT>(i))
-                                             : fmaf(omw, fi[i] - es.x, es.y);
-                    const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
-                                         plane * (unsigned)Z[cz + 1];
-                    if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = from_f<ST>(post);
-                    else                   fout[i * N + dst] = from_f<ST>(post);
-                }
+        for (int a = 0; a < 3; ++a)   // Korteweg force plus the body force rho g
+            F[a] = __fmaf_rn(rho, p.g[a], -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y);
+        // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2, the node's omega
+        const float om = p.var_visc ? omega_var_f(p, rho) : p.omega;
+        const float pref = p.var_visc ? p.phi_sign * (1.0f - 0.5f * om) : p.phi_pref;
+        const float omw = p.var_visc ? 1.0f - om : p.omw;
+        const int gr0 = THREE ? ty + 1 : 0, gc0 = tx + 1;
+        float Phi[3];
+        Phi[0] = pref * 0.5f * (s_g[pc % GS][0][gr0][gc0 + 1] - s_g[pc % GS][0][gr0][gc0 - 1]);
+        Phi[1] = THREE ? pref * 0.5f *
+                             (s_g[pc % GS][1][gr0 + 1][gc0] - s_g[pc % GS][1][gr0 - 1][gc0])
+                       : 0.0f;
+        Phi[2] = pref * 0.5f *
+                 (s_g[(pc + 1) % GS][2][gr0][gc0] - s_g[(pc - 1) % GS][2][gr0][gc0]);
+        // bare velocity and 1/rho of the node, formed by phase A from the same populations
+        const float4 uvn = sm.uv[pc & 3][ty][tx];
+        const float inv = uvn.w;
+        const float un[3] = {uvn.x, uvn.y, uvn.z};
+        // product-form factors, paired (equilibrium, extended)
+        float2 ES[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!THREE && a == 1) {
+                ES[1][0] = ES[1][1] = ES[1][2] = f2(1.0f, 1.0f);
+                continue;
+            }
+            const float ua = un[a];
+            const float ze = 1.0f / 3.0f + ua * ua;
+            const float xs = ua + F[a] * inv;
+            const float zs = 1.0f / 3.0f + xs * xs + Phi[a] * inv;
+            ES[a][0] = f2(0.5f * (ze - ua), 0.5f * (zs - xs));
+            ES[a][1] = f2(1.0f - ze, 1.0f - zs);
+            ES[a][2] = f2(0.5f * (ze + ua), 0.5f * (zs + xs));
+        }
+        float2 A[3][3];
+        const float2 rr = f2(rho, rho);
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+            const float2 rx = __fmul2_rn(rr, ES[0][cx]);
+#pragma unroll
+            for (int cy = 0; cy < 3; ++cy) A[cx][cy] = __fmul2_rn(rx, ES[1][cy]);
+        }
+        // post = f* + (1 - omega)(f - feq), pushed to r + c_i
+        const int X[3] = {wrapf(xi - 1, g.nx), xi, wrapf(xi + 1, g.nx)};
+        const int Y[3] = {THREE ? wrapf(yi - 1, g.ny) : 0, yi, THREE ? wrapf(yi + 1, g.ny) : 0};
+        const int Z[3] = {wrapf(zc - 1, g.nz), zc, wrapf(zc + 1, g.nz)};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
+            const float post = SHIFT ? fmaf(fmaf(omw, fi[i] - es.x, es.y), inv, -weight_f<LAT>(i))
+                                     : fmaf(omw, fi[i] - es.x, es.y);
+            const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
+                                 plane * (unsigned)Z[cz + 1];
+            if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = from_f<ST>(post);
+            else                   fout[i * N + dst] = from_f<ST>(post);
+        }
+    }
+}
+
+// One CTA's work: the column tile (bx, by) over the plane chunk bz. Six
+// (rho, |psi|) slots and five rho u^3 slots let the next plane enter while
+// slower warps still collide: one barrier per plane.
+template <int LAT, bool MASK, typename ST = float, typename SM = SharedF<LAT>>
+__device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
+                                           const uint8_t *__restrict__ mask,
+                                           const ST *__restrict__ f, ST *__restrict__ fout,
+                                           int *__restrict__ status, int bx, int by, int bz,
+                                           SM &sm, const float *__restrict__ rho_src = nullptr,
+                                           float *__restrict__ rho_dst = nullptr)
+{
+    static_assert(!(IsShifted<ST>::value && MASK), "shifted storage runs lattices without solid nodes");
+    constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
+    const int tid = threadIdx.x;
+    const TileF T = tile_setup<LAT, ST>(g, bx, by, bz, sm, tid, NT, rho_src);
+    const bool inside = T.x0 + tid % TX < g.nx && T.y0 + tid / TX < g.ny;
+    __syncthreads();
+    for (int pl = 0; pl < T.np; ++pl) {
+        phase_a<LAT, MASK>(g, p, mask, f, sm, T, pl, tid, rho_src);
+        __syncthreads();
+        if (pl >= 4 && inside) phase_b<LAT, MASK>(g, p, mask, f, fout, status, sm, T, pl, tid, rho_dst);
+    }
+}
+
+// ---- warp-specialised form --------------------------------------------
+// The same tile with two thread groups of NT: producers run phase A, and
+// consumers run phase B, handing planes over through mbarriers instead of a
+// CTA-wide barrier per plane, so the loads and moments of the next planes
+// overlap the collision of the current one.
+//   full[pl % 6] completes when the producers have written ring index pl;
+//     the consumers wait for it before iteration pl (which reads ring
+//     indices up to pl).
+//   empty[j % 6] completes when the consumers have finished iteration j >= 4;
+//     producer iteration pl >= 6 waits for iteration pl - 2, the last reader
+//     of every ring slot that pl overwrites ((rho, |psi|) slot pl % 6 held
+//     pl - 6, read up to iteration pl - 2; rho u^3 slot pl % 5 held pl - 5,
+//     read up to iteration pl - 2; (u, 1/rho) slot pl % 4 held pl - 4, read in
+//     iteration pl - 2).
+// Each barrier completes once per use of its slot, and neither side can get
+// a full cycle ahead of the other, so waiting on the phase parity is exact.
+// Every wait gives up after about a second (kWaitCycles), sets bit 2 of the
+// status word and returns: the step then reports an error instead of hanging.
+constexpr long long kWaitCycles = 2000000000ll;
+
+template <int LAT> struct SharedWS : SharedF<LAT> {
+    unsigned long long full[6], empty[6];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *ptr)
+{
+    return (unsigned)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Arrive with release semantics: this thread's shared-memory writes are
+// visible to a thread whose wait observes the phase completion.
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Wait (acquire) for the completion of the phase of the given parity;
+// false after kWaitCycles without it.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+template <int LAT, bool MASK>
+__device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
+                                              const uint8_t *__restrict__ mask,
+                                              const float *__restrict__ f, float *__restrict__ fout,
+                                              int *__restrict__ status, int bx, int by, int bz,
+                                              SharedWS<LAT> &sm)
+{
+    constexpr int NT = LatF<LAT>::TX * LatF<LAT>::TY;
+    const int tid = threadIdx.x;
+    const TileF T = tile_setup<LAT, float>(g, bx, by, bz, sm, tid, 2 * NT, nullptr);
+    if (tid == 0)
+        for (int k = 0; k < 6; ++k) {
+            mbar_init(&sm.full[k], NT);
+            mbar_init(&sm.empty[k], NT);
+        }
+    __syncthreads();
+    if (tid < NT) {
+        for (int pl = 0; pl < T.np; ++pl) {
+            if (pl >= 6 && !mbar_wait(&sm.empty[(pl - 2) % 6], ((pl - 6) / 6) & 1)) {
+                atomicOr(status, 2);
+                return;
+            }
+            phase_a<LAT, MASK>(g, p, mask, f, sm, T, pl, tid, nullptr);
+            mbar_arrive(&sm.full[pl % 6]);
+        }
+    } else {
+        const int t = tid - NT;
+        constexpr int TX = LatF<LAT>::TX;
+        const bool inside = T.x0 + t % TX < g.nx && T.y0 + t / TX < g.ny;
+        for (int pl = 0; pl < T.np; ++pl) {
+            if (!mbar_wait(&sm.full[pl % 6], (pl / 6) & 1)) {
+                atomicOr(status, 2);
+                return;
+            }
+            if (pl >= 4) {
+                if (inside) phase_b<LAT, MASK>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr);
+                mbar_arrive(&sm.empty[pl % 6]);
             }
         }
     }
+}
+
+// FP32 populations, warp-specialised; 2 TX TY threads, dynamic shared memory
+// of sizeof(SharedWS<LAT>).
+template <int LAT, bool MASK>
+__global__ void __launch_bounds__(2 * LatF<LAT>::TX * LatF<LAT>::TY, 1)
+k_step_f32_ws(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
+              float *__restrict__ fout, int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedWS<LAT> &sm = *reinterpret_cast<SharedWS<LAT> *>(smem_raw);
+    fused_tile_ws<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
 // FP32 populations; dynamic shared memory of sizeof(SharedF<LAT>).

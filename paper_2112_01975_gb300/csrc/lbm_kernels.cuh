@@ -49,7 +49,7 @@ __host__ __device__ constexpr int cxi(int i) { return i % 3 - 1; }
 __host__ __device__ constexpr int cyi(int i) { return (i / 3) % 3 - 1; }
 __host__ __device__ constexpr int czi(int i) { return i / 9 - 1; }
 
-// Pressure of the equations of state of Sec. 3.1 and Appendix C (gas constant 1).
+// Pressure of the equations of state of Sec. 3.1 and Appendix G (gas constant 1).
 __device__ __forceinline__ double eos_pressure(const Phys &p, double rho)
 {
     switch (p.eos) {

@@ -64,6 +64,8 @@ def _load():
     L.lbm_autotune.argtypes = [vp, C.POINTER(C.c_int)]
     L.lbm_get_tile.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lbm_set_tile.argtypes = [vp, C.c_int]
+    L.lbm_set_warp_specialized.argtypes = [vp, C.c_int]
+    L.lbm_get_warp_specialized.argtypes = [vp, C.POINTER(C.c_int)]
     L.lbm_reduce_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.lbm_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
     L.lbm_batch_step.argtypes = [vp, i64]
@@ -99,6 +101,8 @@ lbm_set_chunk = _lib.lbm_set_chunk
 lbm_autotune = _lib.lbm_autotune
 lbm_get_tile = _lib.lbm_get_tile
 lbm_set_tile = _lib.lbm_set_tile
+lbm_set_warp_specialized = _lib.lbm_set_warp_specialized
+lbm_get_warp_specialized = _lib.lbm_get_warp_specialized
 lbm_reduce_noalloc = _lib.lbm_reduce_noalloc
 lbm_batch_create = _lib.lbm_batch_create
 lbm_batch_step = _lib.lbm_batch_step
@@ -292,6 +296,16 @@ class LBM:
     def set_tile(self, tile_y: int):
         """Tile height of the D3Q27 FP32 step: 8 (default) or 7 rows."""
         self._check(_lib.lbm_set_tile(self._h, int(tile_y)))
+
+    def set_warp_specialized(self, on: bool):
+        """Warp-specialised (True) or plain (False) FP32 fused step."""
+        self._check(_lib.lbm_set_warp_specialized(self._h, int(bool(on))))
+
+    @property
+    def warp_specialized(self) -> bool:
+        v = C.c_int()
+        self._check(_lib.lbm_get_warp_specialized(self._h, C.byref(v)))
+        return bool(v.value)
 
     def tile(self):
         """(tile_x, tile_y) of the fused step in use; (0, 0) for FP64."""

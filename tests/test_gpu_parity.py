@@ -217,6 +217,31 @@ def test_nonfinite_density_is_reported_and_blocks_steps(lbm):
     g.sync(5000)
 
 
+@pytest.mark.parametrize("storage", [0, 1])
+def test_long_step_call_stops_at_a_nonfinite_density(lbm, storage):
+    """lbm_step polls the status word every 64 steps: a NaN planted in the
+    initial density (from the host) stops a 4000-step call within two
+    polling intervals with LBM_ENONFINITE from lbm_step itself, and the
+    launches after it are not issued."""
+    g = lbm.LBM(0, 16, 16, 1, 0, 0.8, 0.02, 1.0, a=9 / 490, storage=storage)
+    r = np.full(256, 2.0)
+    r[37] = np.nan
+    g.init(r)
+    l0 = g.launches
+    with pytest.raises(lbm.LBMError) as e:
+        g.step(4000)
+    assert e.value.code == 4
+    per_step = 2 if storage == 0 else 1
+    assert g.launches - l0 <= per_step * (3 * 64 + 2)
+    with pytest.raises(lbm.LBMError) as e:
+        g.step(1)
+    assert e.value.code == 6
+    g.init(np.full(256, 2.0))
+    g.step(4000)                   # a healthy state runs through the polls
+    g.sync(5000)
+    assert g.launches - l0 >= per_step * 4000
+
+
 def test_phi_off_flag_matches_oracle(lbm):
     from oracle.lbm import PHI_OFF
     nx = 64

@@ -79,3 +79,35 @@ def test_noalloc_rejects_sizes_beyond_its_maximum(env):
                                 C.c_void_p(out.data_ptr()), None)
     assert rc == 7                                          # LBM_ETOOBIG
     assert out.abs().sum().item() == 0.0
+
+
+def test_noalloc_allocates_nothing(env):
+    """After a first (warm) call, five more calls leave the device's free
+    memory (cudaMemGetInfo) and the torch allocator's counters unchanged:
+    the entry point allocates nothing on the device."""
+    torch, lbm, inputs = env
+    v = inputs.DROP_D2Q9_64
+    g = lbm.LBM(0, 64, 64, 1, v.eos, v.t_over_tc, v.kappa, v.tau, a=v.a, b=v.b)
+    g.init(v.rho0())
+    f_dev = torch.empty(g.Q * g.N, dtype=torch.float64, device="cuda")
+    g.get_populations(f_dev)
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def call():
+        rc = lbm.lbm_reduce_noalloc(0, 64, 64, 1, C.c_void_p(f_dev.data_ptr()), None,
+                                    C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
+        assert rc == 0
+
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(5):
+        call()
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
