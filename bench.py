@@ -57,7 +57,7 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (an FMA-chain probe measured
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per lattice node
 # of one launch of the fused step, from an ncu capture of the named workload
 # (scaled to the capture's lattice, as stated), keyed by (workload, storage,
-# tile rows, warp-specialised); each entry records the SHA-256 prefix of the fused kernel's
+# tile rows, fused-step form); each entry records the SHA-256 prefix of the fused kernel's
 # source it was taken on, and is not used once that source has changed.
 MEASURED_TRAFFIC = {}
 FUSED_SRC = os.path.join(ROOT, "paper_2112_01975_gb300", "csrc", "lbm_fused_f32_body.cuh")
@@ -69,9 +69,9 @@ def fused_src_sha() -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def measured_traffic(name: str, storage: str, rows: int, ws: bool, nodes: int):
+def measured_traffic(name: str, storage: str, rows: int, variant: int, nodes: int):
     """ncu DRAM bytes of one launch scaled to `nodes`, or None."""
-    v = MEASURED_TRAFFIC.get((name, storage, rows, ws))
+    v = MEASURED_TRAFFIC.get((name, storage, rows, variant))
     if v is None or v["src_sha"] != fused_src_sha():
         return None
     return v["bytes_per_node"] * nodes
@@ -90,10 +90,13 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 7, 8],
                     help="D3Q27 FP32 tile height (0: picked by the autotuner, or 8 with --chunk)")
-    ap.add_argument("--ws", type=int, default=-1, choices=[-1, 0, 1],
-                    help="FP32 warp-specialised kernel (-1: picked by the autotuner, or plain with --chunk)")
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="FP32 fused-step form: 0 plain, 1 warp-specialised, 2 Tensor Memory "
+                         "(-1: picked by the autotuner, or plain with --chunk)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--eos64", action="store_true",
+                    help="reduced storage with the EOS and force sums in FP64 (LBM_FLAG_EOS_F64)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving sweep reported under \"serve\"")
     ap.add_argument("--mode", default="step", choices=["step", "serve", "validate"],
@@ -210,7 +213,7 @@ def sample_shape(w, kind: str):
     if w.lattice == 0:
         return (64, 64, 1)
     if w.mask_seed is not None:   # the impact keeps its pillars and gap: a 1/4 or 1/6 box
-        return (96, 96, 64) if kind == "cpu" else (48, 48, 40)
+        return (96, 96, 64) if kind == "cpu" else (48, 48, 48)
     return (48, 48, 48) if kind == "cpu" else (32, 32, 32)
 
 
@@ -407,10 +410,11 @@ def _validate_cfg3(L, torch, storage, steps, every=1000):
     a = eos_tables.stable_a(1, tr)
     rv, rl, _ = eos_tables.coexistence(1, tr, a)
     kap = eos_tables.kappa_for_width(1, tr, a, width=5.0)
-    st = {"f64": L.F64, "f32": L.F32, "f16s": L.F16S, "bf16s": L.BF16S}[storage]
+    flags = L.FLAG_EOS_F64 if storage.endswith("e64") else 0
+    st = {"f64": L.F64, "f32": L.F32, "f16s": L.F16S, "bf16s": L.BF16S}[storage.replace("e64", "")]
     centres = [(n // 2 - R, n // 2, n // 2), (n // 2 + R, n // 2, n // 2)]
     rho0 = inputs.add_noise(inputs.drops(n, n, n, centres, R, rv, rl, width=5.0), 1e-4, 3)
-    g = L.LBM(1, n, n, n, 1, tr, kap, 0.725, a=a, storage=st)
+    g = L.LBM(1, n, n, n, 1, tr, kap, 0.725, a=a, storage=st, flags=flags)
     g.init(rho0)
     m0, _ = g.reduce()
     rho_t = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
@@ -436,35 +440,35 @@ def _validate_cfg3(L, torch, storage, steps, every=1000):
 
 
 def _validate_cfg4(L, steps, every=2000):
-    """A PR drop of radius 60 moving down at U = 0.05 onto 8x8x16 pillars
-    (pitch 16) on a wall, 384x384x256, T/Tc 0.5, tau 0.725, FP32: mass
-    drift, the liquid area just above the pillar tops and the height of the
-    liquid's centre of mass over time, and the last step reached."""
-    from paper_2112_01975_gb300 import eos_tables, inputs
-    tr, (nx, ny, nz), R, U = 0.5, (384, 384, 256), 60.0, 0.05
-    a = eos_tables.stable_a(1, tr)
-    rv, rl, _ = eos_tables.coexistence(1, tr, a)
-    kap = eos_tables.kappa_for_width(1, tr, a, width=5.0)
-    mask = inputs.pillar_mask(nx, ny, nz, seed=4)
-    drop = inputs.drop(nx, ny, nz, R, rv, rl, width=5.0, center=(nx // 2, ny // 2, 16 + R + 8))
-    u0 = np.zeros(3 * drop.size)
-    u0[2 * drop.size:] = np.where(mask == 1, 0.0, -U * (drop - rv) / (rl - rv))
-    g = L.LBM(1, nx, ny, nz, 1, tr, kap, 0.725, mask=mask, a=a, rho_w=rv, storage=L.F32)
-    g.init(np.where(mask == 1, rv, drop), u0)
+    """The impact workload (inputs.IMPACT_D3Q27_384: a drop of radius 60 at
+    U = 0.115, We = 100, onto 8x8x16 pillars on a two-plane wall,
+    384x384x256, PR T/Tc 0.5, tau 0.725, FP32): mass drift, the liquid area
+    just above the pillar tops and the height of the liquid's centre of mass
+    over time, and the last step reached."""
+    from paper_2112_01975_gb300 import inputs
+    w = inputs.IMPACT_D3Q27_384
+    nx, ny, nz = w.nx, w.ny, w.nz
+    rv, rl = w.rho_v, w.rho_l
+    rho0, u0, mask = w.fields()
+    g = L.LBM(1, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, w.tau, mask=mask, a=w.a, b=w.b,
+              rho_w=w.rho_w, storage=L.F32)
+    g.init(rho0, u0)
     m0, _ = g.reduce()
+    zt = w.wall + w.pillar[1]
     wet, t0, failed = [], time.perf_counter(), None
     for s in range(every, steps + 1, every):
-        g.step(every)
         try:
+            g.step(every)
             rho = g.moments()[0].reshape(nz, ny, nx)
         except L.LBMError as exc:
             failed = f"step <= {s}: {exc}"
             break
         liq = rho > 0.5 * (rl + rv)
         zc = float((np.arange(nz)[:, None, None] * liq).sum() / max(liq.sum(), 1))
-        wet.append((s, float(np.sqrt(np.count_nonzero(liq[17]) / np.pi)), zc))
+        wet.append((s, float(np.sqrt(np.count_nonzero(liq[zt]) / np.pi)), zc))
     dt = time.perf_counter() - t0
-    out = {"steps": steps, "step_wetted_radius_z17_liquid_z": wet, "failed": failed}
+    out = {"steps": steps, "U": w.u_down, "tau": w.tau, "wall_planes": w.wall,
+           "step_wetted_radius_above_pillars_liquid_z": wet, "failed": failed}
     if failed is None:
         m1, _ = g.reduce()
         out["mass_drift"] = m1 / m0 - 1.0
@@ -533,9 +537,12 @@ def main():
     rho0, u0, mask = w.fields(shape)
     D = 3 if w.lattice else 2
 
+    from paper_2112_01975_gb300.lbm import FLAG_EOS_F64
+
     def make(st):
         return LBM(w.lattice, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, w.tau, mask=mask, a=w.a,
-                   b=w.b, rho_w=w.rho_w, stream=stream, storage=st)
+                   b=w.b, rho_w=w.rho_w, stream=stream, storage=st,
+                   flags=FLAG_EOS_F64 if args.eos64 and st != F64 else 0)
 
     g = make(storage)
     g.init(rho0, u0)
@@ -545,8 +552,8 @@ def main():
         g.set_chunk(chunk)
         if args.tile and storage == F32 and w.lattice == 1:
             g.set_tile(args.tile)
-        if args.ws >= 0 and storage == F32:
-            g.set_warp_specialized(bool(args.ws))
+        if args.variant >= 0 and storage == F32:
+            g.set_fused_variant(args.variant)
     g.step(args.warmup)
     g.sync()
     with ClockSampler(local) as clocks:
@@ -564,16 +571,18 @@ def main():
     alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * nodes
     per_step = launches / args.steps if args.steps else 1
     tile = g.tile()
-    ws = storage == F32 and g.warp_specialized
+    variant = g.fused_variant if storage == F32 else 0
     if storage != F64:
         ms_launch = ms / max(launches, 1)
         achieved = alg / (ms_launch * 1e-3) / 1e9
-        traffic = measured_traffic(w.name, args.storage, tile[1], ws, nodes) if per_step == 1 else None
+        traffic = measured_traffic(w.name, args.storage, tile[1], variant, nodes) if per_step == 1 else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "frac_of_nominal_7900_gbs": achieved / 7900.0,
-                    "kernel": ("k_step_f32_ws (fused step, warp-specialised)" if ws else
-                               "k_step_f32 (fused step)") if storage == F32 else "k_step_shifted",
+                    "kernel": {0: "k_step_f32 (fused step)",
+                               1: "k_step_f32_ws (fused step, warp-specialised)",
+                               2: "k_step_f32_tm (fused step, Tensor Memory staging)"}[variant]
+                    if storage == F32 else "k_step_shifted",
                     "peak_source": peak_kind + " hbm_gbs (burst copy)",
                     "alg_bytes_per_launch": alg, "ms_per_launch": ms_launch,
                     "ms_per_launch_source": "CUDA events over the timed graph replays / launches",
@@ -656,7 +665,8 @@ def main():
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "vs_baseline": None, "dtype": args.storage + ("+eos64" if args.eos64 else ""),
+        "data": "synthetic",
         "config": {"workload": w.name if not args.shape else f"{w.name} scaled to {args.shape}",
                    "lattice": "D3Q27" if w.lattice else "D2Q9", "shape": [nx, ny, nz],
                    "nodes": nodes, "storage": args.storage,

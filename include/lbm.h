@@ -92,7 +92,17 @@ enum lbm_status {
 };
 
 /* Flags of lbm_params.flags. */
-enum { LBM_FLAG_PHI_OFF = 1 /* drop the correction Phi (Eq. correction) */ };
+enum {
+    LBM_FLAG_PHI_OFF = 1,  /* drop the correction Phi (Eq. correction) */
+    /* Reduced storage (LBM_F32, LBM_F16S, LBM_BF16S): evaluate the EOS, the
+     * pseudo-potential psi = sqrt|P - P0| and the force's stencil sums and
+     * combination in FP64 inside the fused step (populations, moments and
+     * the collision stay FP32). Meant for deep-subcritical states, where P
+     * and rho/3 nearly cancel in the vapour and 1 - b rho is small in the
+     * liquid. Runs the plain 32 x 8 form only (no other variant or tile, no
+     * batches: LBM_EINVAL), at the GPU's FP64 rate. No effect on LBM_F64. */
+    LBM_FLAG_EOS_F64 = 2
+};
 
 /* EOS constants and options. a, b: EOS attraction and co-volume (lattice
  * units, R = 1); acentric: acentric factor of PR/RKS (Sec. 3.1); rho_w:
@@ -245,14 +255,14 @@ int lbm_set_chunk(lbm_handle h, int chunk);
  * handle's own state (saved to a temporary device buffer and restored
  * afterwards, so the state is unchanged). Sets and returns it in
  * *chunk_out (0 for FP64 storage, which has no tile parameter). With
- * LBM_F32 storage it also picks between the plain and the warp-specialised
- * kernel (lbm_set_warp_specialized), and for D3Q27 the tile height, 8 or 7
+ * LBM_F32 storage it also picks the form of the step
+ * (lbm_set_fused_variant), and for D3Q27 the tile height, 8 or 7
  * rows of 32 nodes (7 rows fill every SM with two CTAs in one wave where 8
  * rows leave some SMs with one, e.g. at 128^3); the shifted storages and
- * batches keep the plain kernel with 8 rows. Kernels, tiles and chunks
+ * batches keep the plain form with 8 rows. Forms, tiles and chunks
  * change the work split only: results are bitwise the same. Synchronising;
  * allocates and frees one state-sized buffer; on failure the handle keeps
- * the kernel, tile and chunk it had. */
+ * the form, tile and chunk it had. */
 int lbm_autotune(lbm_handle h, int *chunk_out);
 
 /* The tile of the fused step in use, in nodes: *tile_x = 32, *tile_y = 8 or
@@ -267,20 +277,31 @@ int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y);
  * storage. */
 int lbm_set_tile(lbm_handle h, int tile_y);
 
-/* Select the warp-specialised form of the LBM_F32 fused step (on != 0) or
- * the plain one (0, the default). The warp-specialised kernel runs two
- * thread groups per tile: one forms each entering plane's densities,
- * pseudo-potentials and velocities (the first half of the step), the other
- * collides and streams the plane two behind it, and the groups hand planes
- * over through shared-memory barriers instead of a barrier of the whole
- * block per plane. Same arithmetic in the same order: results are bitwise
- * those of the plain kernel. A wait between the groups that does not end
- * within about a second (a fault, never normal operation) makes the next
- * synchronising call return LBM_ETIMEOUT. LBM_EINVAL for other storage. */
-int lbm_set_warp_specialized(lbm_handle h, int on);
+/* Forms of the LBM_F32 fused step; the same arithmetic in the same order,
+ * so results are bitwise the same whichever runs.
+ *   LBM_FUSED_PLAIN (default): one thread group per tile; each entering
+ *     plane's densities, pseudo-potentials and velocities are formed, the
+ *     block synchronises, and the plane two behind collides and streams,
+ *     reading its node's populations again (an L2 hit).
+ *   LBM_FUSED_WARP_SPECIALISED: two thread groups per tile, one forming the
+ *     entering planes and one colliding, handing planes over through
+ *     shared-memory barriers instead of a barrier of the whole block per
+ *     plane. A wait between the groups that does not end within about a
+ *     second (a fault, never normal operation) makes the next synchronising
+ *     call return LBM_ETIMEOUT.
+ *   LBM_FUSED_TMEM: the plain form, with each node's populations kept in the
+ *     SM's Tensor Memory from the plane's entry to its collision instead of
+ *     being read twice; each block holds 256 columns (D3Q27; 64 for D2Q9) of
+ *     Tensor Memory while it runs. */
+enum { LBM_FUSED_PLAIN = 0, LBM_FUSED_WARP_SPECIALISED = 1, LBM_FUSED_TMEM = 2 };
 
-/* *on = 1 if the warp-specialised LBM_F32 step is selected, else 0. */
-int lbm_get_warp_specialized(lbm_handle h, int *on);
+/* Select a form of the LBM_F32 fused step (lbm_autotune times all three).
+ * LBM_EINVAL for an unknown form, or a form other than LBM_FUSED_PLAIN with
+ * another storage. */
+int lbm_set_fused_variant(lbm_handle h, int variant);
+
+/* *variant = the form of the fused step in use. */
+int lbm_get_fused_variant(lbm_handle h, int *variant);
 
 /* ---- Batches: many lattices advanced by one persistent launch ----------
  * A batch holds count >= 1 distinct, initialised handles with the same

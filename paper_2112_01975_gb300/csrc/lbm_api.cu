@@ -29,7 +29,8 @@ struct lbm_ctx {
     GeoF geof;     // FP32 fused step: 3D frame (D2Q9: ny = 1, nz = 2D y extent)
     PhysF physf;
     int tile_rows = 8;   // D3Q27 FP32 step: 32 x 8 (lbmf) or 32 x 7 (lbmf7) tiles
-    bool ws = false;     // FP32 step: warp-specialised kernel (k_step_f32_ws)
+    int variant = LBM_FUSED_PLAIN;   // FP32 step: plain, warp-specialised or Tensor Memory form
+    bool e64 = false;    // reduced storage: EOS, psi and force sums in FP64 (LBM_FLAG_EOS_F64)
     int storage, flags;
     double t_over_tc, tau;
     std::vector<uint8_t> mask_host;
@@ -178,6 +179,27 @@ double eos_alpha(int eos, double acentric, double tr)
     return s * s;
 }
 
+// P - rho/3 in FP64 on the host (the EOS of the solid nodes' virtual density
+// for the FP64-EOS form of the reduced-precision steps).
+double excess_pressure_host(int eos, double a, double b, double RT, double aalpha, double r)
+{
+    const double br = b * r, rt = r * RT;
+    double P;
+    switch (eos) {
+    case LBM_EOS_VDW: P = rt / (1.0 - br) - a * r * r; break;
+    case LBM_EOS_PR: P = (rt * (1.0 + br * (2.0 - br)) - aalpha * r * r * (1.0 - br)) /
+                         ((1.0 - br) * (1.0 + br * (2.0 - br))); break;
+    case LBM_EOS_RKS: P = (rt * (1.0 + br) - aalpha * r * r * (1.0 - br)) / ((1.0 - br) * (1.0 + br)); break;
+    case LBM_EOS_SC1: { const double q = 1.0 - std::exp(-r); P = r / 3.0 + RT / 6.0 * q * q; break; }
+    case LBM_EOS_SC2: { const double q = std::exp(-1.0 / r); P = r / 3.0 + RT / 6.0 * q * q; break; }
+    default: {
+        const double e = 0.25 * br, om = 1.0 - e;
+        P = rt * (1.0 + e + e * e - e * e * e) / (om * om * om) - a * r * r;
+    }
+    }
+    return P - r / 3.0;
+}
+
 dim3 node_block(const Geo &g)
 {
     int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
@@ -252,7 +274,16 @@ template <bool MASK>
 void launch_fused_r7(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
     using L = lbmf7::LatF<1>;
-    if (h->ws) {
+    if (h->variant == LBM_FUSED_TMEM) {
+        static std::atomic<unsigned long long> done{0};   // devices already opted in
+        const int bytes = (int)sizeof(lbmf7::SharedF<1>);
+        smem_opt_in(lbmf7::k_step_f32_tm<1, MASK>, bytes, done);
+        lbmf7::k_step_f32_tm<1, MASK><<<fused_grid<1>(h->geof, L::TY), L::TX * L::TY, bytes, s>>>(
+            as_layout<lbmf7::GeoF>(h->geof), as_layout<lbmf7::PhysF>(h->physf), h->mask, src, dst,
+            h->status);
+        return;
+    }
+    if (h->variant == LBM_FUSED_WARP_SPECIALISED) {
         static std::atomic<unsigned long long> done{0};   // devices already opted in
         const int bytes = (int)sizeof(lbmf7::SharedWS<1>);
         smem_opt_in(lbmf7::k_step_f32_ws<1, MASK>, bytes, done);
@@ -270,6 +301,17 @@ void launch_fused_r7(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 }
 
 template <int LAT, bool MASK>
+void launch_fused_tm(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    using L = lbmf::LatF<LAT>;
+    const int bytes = (int)sizeof(lbmf::SharedF<LAT>);
+    smem_opt_in(lbmf::k_step_f32_tm<LAT, MASK>, bytes, done);
+    lbmf::k_step_f32_tm<LAT, MASK><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, src, dst, h->status);
+}
+
+template <int LAT, bool MASK>
 void launch_fused_ws(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
     static std::atomic<unsigned long long> done{0};   // devices already opted in
@@ -280,17 +322,38 @@ void launch_fused_ws(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
         h->geof, h->physf, h->mask, src, dst, h->status);
 }
 
+template <int LAT, bool MASK>
+void launch_fused_e64(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    using L = lbmf::LatF<LAT>;
+    const int bytes = (int)sizeof(lbmf::SharedF<LAT>);
+    smem_opt_in(lbmf::k_step_f32<LAT, MASK, true>, bytes, done);
+    lbmf::k_step_f32<LAT, MASK, true><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, src, dst, h->status);
+}
+
 template <int LAT>
 void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
+    if (h->e64) {   // the plain 32 x 8 form only
+        if (has_solid(h)) launch_fused_e64<LAT, true>(h, s, src, dst);
+        else              launch_fused_e64<LAT, false>(h, s, src, dst);
+        return;
+    }
     if (LAT == 1 && h->tile_rows == 7) {
         if (has_solid(h)) launch_fused_r7<true>(h, s, src, dst);
         else              launch_fused_r7<false>(h, s, src, dst);
         return;
     }
-    if (h->ws) {
+    if (h->variant == LBM_FUSED_WARP_SPECIALISED) {
         if (has_solid(h)) launch_fused_ws<LAT, true>(h, s, src, dst);
         else              launch_fused_ws<LAT, false>(h, s, src, dst);
+        return;
+    }
+    if (h->variant == LBM_FUSED_TMEM) {
+        if (has_solid(h)) launch_fused_tm<LAT, true>(h, s, src, dst);
+        else              launch_fused_tm<LAT, false>(h, s, src, dst);
         return;
     }
     static std::atomic<unsigned long long> done_m{0}, done_f{0};   // devices already opted in
@@ -308,16 +371,23 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
     }
 }
 
-template <int LAT, typename ST>
-void launch_shifted_t(lbm_ctx *h, cudaStream_t s, int k)
+template <int LAT, typename ST, bool E64>
+void launch_shifted_e(lbm_ctx *h, cudaStream_t s, int k)
 {
     static std::atomic<unsigned long long> done{0};   // devices already opted in
     const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
-    smem_opt_in(lbmf::k_step_shifted<LAT, ST>, bytes, done);
+    smem_opt_in(lbmf::k_step_shifted<LAT, ST, E64>, bytes, done);
     using L = lbmf::LatF<LAT>;
-    lbmf::k_step_shifted<LAT, ST><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
+    lbmf::k_step_shifted<LAT, ST, E64><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
         h->geof, h->physf, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
         h->rs[k], h->rs[k ^ 1], h->status);
+}
+
+template <int LAT, typename ST>
+void launch_shifted_t(lbm_ctx *h, cudaStream_t s, int k)
+{
+    if (h->e64) launch_shifted_e<LAT, ST, true>(h, s, k);
+    else        launch_shifted_e<LAT, ST, false>(h, s, k);
 }
 
 template <int LAT>
@@ -738,6 +808,12 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     pf.visc_rl = (float)ph.visc_rl;
     pf.inv_drho = ph.var_visc ? (float)(1.0 / (ph.visc_rl - ph.visc_rv)) : 0.0f;
     pf.phi_sign = (float)ph.phi_sign;
+    pf.da = ph.a;
+    pf.db = ph.b;
+    pf.dRT = ph.RT;
+    pf.daalpha = ph.a * ph.alpha;
+    pf.dkappa = kappa;
+    h->e64 = (prm.flags & LBM_FLAG_EOS_F64) != 0;
     {
         // P - P0 of the solid density, in FP32
         const float r = pf.rho_w;
@@ -764,6 +840,7 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
         }
         const float d = P - r * (1.0f / 3.0f);
         pf.spsi_w = d;
+        if (h->e64) pf.spsi_w = (float)excess_pressure_host(eos, ph.a, ph.b, ph.RT, ph.a * ph.alpha, prm.rho_w);
     }
     h->mask_host.assign(h->geo.N, 0);
     if (solid_mask)
@@ -1154,7 +1231,8 @@ int lbm_batch_create(lbm_batch *out, const lbm_handle *members, int count)
     for (int k = 0; k < count; ++k) {
         lbm_ctx *h = members[k];
         if (!h || !h->initialised || h->bad || h->storage != storage || h->lattice != lattice ||
-            h->nb > 0)   // interpolated bounce-back is not part of the batched step
+            h->nb > 0 ||   // interpolated bounce-back is not part of the batched step
+            h->e64)        // nor the FP64-EOS form
             return LBM_EINVAL;
         for (int j = 0; j < k; ++j)
             if (members[j] == h) return LBM_EINVAL;   // a lattice at most once
@@ -1375,16 +1453,16 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128};
     const int nz = h->geof.nz;
     const int chunk0 = h->geof.chunk, rows0 = h->tile_rows;   // restored on failure
-    // FP32: the plain and the warp-specialised kernel; D3Q27 FP32 also 32 x 8
-    // and 32 x 7 tiles (the shifted and batched steps use plain 32 x 8)
-    const bool fp32 = h->storage == LBM_F32;
+    // FP32: the plain, warp-specialised and Tensor Memory kernels; D3Q27 FP32
+    // also 32 x 8 and 32 x 7 tiles (the shifted and batched steps use plain
+    // 32 x 8)
+    const bool fp32 = h->storage == LBM_F32 && !h->e64;   // the FP64-EOS form is plain 32 x 8
     const bool two_heights = h->lattice == LBM_D3Q27 && fp32;
-    const bool ws0 = h->ws;
-    int best = h->geof.chunk, best_rows = h->tile_rows;
-    bool best_ws = h->ws;
+    const int variant0 = h->variant;
+    int best = h->geof.chunk, best_rows = h->tile_rows, best_variant = h->variant;
     double best_ms = 1e30;
-    for (int spec = 0; spec < (fp32 ? 2 : 1) && rc == LBM_OK; ++spec) {
-        h->ws = spec == 1;
+    for (int var = 0; var < (fp32 ? 3 : 1) && rc == LBM_OK; ++var) {
+        h->variant = var;
         for (int rows : {8, 7}) {
             if (rows == 7 && !two_heights) continue;
             h->tile_rows = rows;
@@ -1395,7 +1473,7 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
                 rc = lbm_time_kernels(h, 1, ms);                  // warm-up
                 if (rc == LBM_OK) rc = lbm_time_kernels(h, 6, ms);
                 if (rc != LBM_OK) break;
-                if (ms[1] < best_ms) { best_ms = ms[1]; best = c; best_rows = rows; best_ws = h->ws; }
+                if (ms[1] < best_ms) { best_ms = ms[1]; best = c; best_rows = rows; best_variant = var; }
             }
             if (rc != LBM_OK) break;
         }
@@ -1404,7 +1482,7 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     // had; a graph captured before the search may hold either, so it is dropped
     h->tile_rows = rc == LBM_OK ? best_rows : rows0;
     h->geof.chunk = rc == LBM_OK ? best : chunk0;
-    h->ws = rc == LBM_OK ? best_ws : ws0;
+    h->variant = rc == LBM_OK ? best_variant : variant0;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -1442,6 +1520,7 @@ int lbm_set_tile(lbm_handle h, int tile_y)
     if (h->lattice != LBM_D3Q27 || h->storage != LBM_F32)
         return fail(h, LBM_EINVAL, "the tile height is a parameter of the D3Q27 FP32 step only");
     if (tile_y != 7 && tile_y != 8) return fail(h, LBM_EINVAL, "tile height must be 7 or 8");
+    if (tile_y == 7 && h->e64) return fail(h, LBM_EINVAL, "the FP64-EOS step runs 8-row tiles");
     if (h->tile_rows != tile_y && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -1450,23 +1529,26 @@ int lbm_set_tile(lbm_handle h, int tile_y)
     return LBM_OK;
 }
 
-int lbm_set_warp_specialized(lbm_handle h, int on)
+int lbm_set_fused_variant(lbm_handle h, int variant)
 {
     if (!h) return LBM_EINVAL;
-    if (h->storage != LBM_F32)
-        return fail(h, LBM_EINVAL, "the warp-specialised kernel is a form of the FP32 step only");
-    if (h->ws != (on != 0) && h->graph) {   // the captured graph holds the other kernel
+    if (variant < LBM_FUSED_PLAIN || variant > LBM_FUSED_TMEM)
+        return fail(h, LBM_EINVAL, "unknown fused-step variant %d", variant);
+    if ((h->storage != LBM_F32 || h->e64) && variant != LBM_FUSED_PLAIN)
+        return fail(h, LBM_EINVAL, "the fused-step variants are forms of the FP32 step only "
+                                   "(without LBM_FLAG_EOS_F64)");
+    if (h->variant != variant && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
-    h->ws = on != 0;
+    h->variant = variant;
     return LBM_OK;
 }
 
-int lbm_get_warp_specialized(lbm_handle h, int *on)
+int lbm_get_fused_variant(lbm_handle h, int *variant)
 {
-    if (!h || !on) return LBM_EINVAL;
-    *on = h->ws ? 1 : 0;
+    if (!h || !variant) return LBM_EINVAL;
+    *variant = h->variant;
     return LBM_OK;
 }
 

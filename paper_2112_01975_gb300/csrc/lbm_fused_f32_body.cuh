@@ -60,6 +60,9 @@ struct PhysF {
     float g[3];                         // body acceleration in the kernel frame (D2Q9: gx, 0, gy)
     int var_visc;                       // density-dependent relaxation (nu linear in rho)
     float nu_l, nu_v, visc_rl, inv_drho, phi_sign;   // inv_drho = 1 / (rho_l - rho_v)
+    // FP64 constants of the EOS and the capillary term, for the kernels that
+    // evaluate the EOS and the force in FP64 (lbm_params.flags & LBM_FLAG_EOS_F64)
+    double da, db, dRT, daalpha, dkappa;
 };
 
 // Relaxation rate at density rho: nu from nu_l at rho_l to nu_v at rho_v,
@@ -131,6 +134,37 @@ __device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
     }
 }
 
+// P - rho/3 in FP64: the same equations of state, for the FP64-EOS form of
+// the reduced-precision steps (Sec. 3.1 and Appendix G).
+__device__ __forceinline__ double excess_pressure_d(const PhysF &p, double rho)
+{
+    const double br = p.db * rho, rr = rho * rho, rt = rho * p.dRT;
+    switch (p.eos) {
+    case 0:
+        return rt / (1.0 - br) - p.da * rr - rho * (1.0 / 3.0);
+    case 1: {
+        const double d1 = 1.0 - br, d2 = 1.0 + br * (2.0 - br);
+        return (rt * d2 - p.daalpha * rr * d1) / (d1 * d2) - rho * (1.0 / 3.0);
+    }
+    case 2: {
+        const double d1 = 1.0 - br, d2 = 1.0 + br;
+        return (rt * d2 - p.daalpha * rr * d1) / (d1 * d2) - rho * (1.0 / 3.0);
+    }
+    case 4: {
+        const double q = 1.0 - exp(-rho);
+        return p.dRT * (1.0 / 6.0) * q * q;
+    }
+    case 5: {
+        const double q = exp(-1.0 / rho);
+        return p.dRT * (1.0 / 6.0) * q * q;
+    }
+    default: {
+        const double e = 0.25 * br, om = 1.0 - e;
+        return rt * (1.0 + e + e * e - e * e * e) / (om * om * om) - p.da * rr - rho * (1.0 / 3.0);
+    }
+    }
+}
+
 __device__ __forceinline__ int wrapf(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -148,6 +182,7 @@ template <int LAT> struct SharedF {
     float g[GS][3][GY][GX];  // rho u_a^3
     int xw[AX], yw[AY];      // wrapped halo coordinates
     float4 uv[4][TY][TX];    // (u_x, u_y, u_z, 1/rho) of the interior nodes, from phase A
+    unsigned tmem;           // Tensor Memory base address (k_step_f32_tm)
 };
 
 // Shifted 16-bit storage also keeps the source densities of the planes in
@@ -186,6 +221,118 @@ __device__ __forceinline__ void load_rho_plane(SM &sm, const GeoF &g, const floa
         sm.rs[(q + QS) & (QS - 1)][r][c] =
             __ldg(rho_src + ((unsigned)sm.rxw[c] + (unsigned)g.nx * (unsigned)sm.ryw[r] + plane * (unsigned)zq));
     }
+}
+
+// Shared-memory address of a generic pointer into shared memory.
+__device__ __forceinline__ unsigned smem_u32(const void *ptr)
+{
+    return (unsigned)__cvta_generic_to_shared(ptr);
+}
+
+// ---- Tensor Memory staging of a node's populations --------------------
+// Phase A loads every interior node's populations (its thread's first halo
+// node) and phase B, two planes later, needs them again. Instead of a
+// second read through L2, the thread keeps them in its own lane of the
+// SM's Tensor Memory (tcgen05.st / tcgen05.ld, 32 x 32-bit per lane and
+// column), three plane slots deep. Warp w reaches lanes 32 (w % 4) ..
+// 32 (w % 4) + 31, so warps w and w + 4 share lanes and take separate
+// column ranges. The block allocates TmemF::COLS columns (256 for D3Q27
+// tiles, two blocks per SM fill the 512) and frees them before it exits.
+template <int LAT> struct TmemF {
+    static constexpr int Q = LatF<LAT>::Q;
+    static constexpr int CPS = Q <= 16 ? 16 : 32;          // columns per plane slot
+    static constexpr int SLOTS = 3;
+    static constexpr int WARPS = LatF<LAT>::TX * LatF<LAT>::TY / 32;
+    static constexpr int NEED = (WARPS + 3) / 4 * SLOTS * CPS;
+    static constexpr int COLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
+};
+
+// Tensor Memory address of this thread's lane, plane slot `slot`.
+template <int LAT>
+__device__ __forceinline__ unsigned tmem_slot(unsigned base, int slot)
+{
+    using T = TmemF<LAT>;
+    const int w = threadIdx.x >> 5;
+    return base + ((unsigned)(32 * (w & 3)) << 16) + (unsigned)((w >> 2) * T::SLOTS * T::CPS + slot * T::CPS);
+}
+
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Allocate ncols columns (one warp, all lanes); the base address lands in *dst.
+__device__ __forceinline__ void tmem_alloc(unsigned *dst, unsigned ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n\t"
+                 "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;"
+                 ::"r"(smem_u32(dst)), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(unsigned base, unsigned ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+// Store the first Q of v into this thread's lane at taddr (whole warp), and
+// wait for the store to complete.
+template <int Q>
+__device__ __forceinline__ void tmem_store_pop(unsigned taddr, const float *f)
+{
+    constexpr int N = Q <= 16 ? 16 : 32;
+    unsigned v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = __float_as_uint(f[i < Q ? i : 0]);
+    if constexpr (N == 32)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n\ttcgen05.wait::st.sync.aligned;" ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]) : "memory");
+    else
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};\n\ttcgen05.wait::st.sync.aligned;" ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
+}
+
+// Load Q values of this thread's lane at taddr (whole warp).
+template <int Q>
+__device__ __forceinline__ void tmem_load_pop(unsigned taddr, float *f)
+{
+    constexpr int N = Q <= 16 ? 16 : 32;
+    unsigned v[N];
+    if constexpr (N == 32)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\ttcgen05.wait::ld.sync.aligned;" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]) : "r"(taddr) : "memory");
+    else
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]) : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = __uint_as_float(v[i]);
+}
+
+// Halo node k of a tile, interior nodes first: k < NT is the interior node
+// (k / TX, k % TX), so a thread's first halo node is the node it collides in
+// phase B; then the 2-node border: the HY top rows, the HY bottom rows, and
+// two columns on either side of each interior row.
+template <int LAT>
+__device__ __forceinline__ void halo_rc(int k, int &r, int &c)
+{
+    using L = LatF<LAT>;
+    constexpr int TX = L::TX, TY = L::TY, HY = L::HY, NT = TX * TY;
+    constexpr int AX = SharedF<LAT>::AX, AY = SharedF<LAT>::AY;
+    if (k < NT) {
+        r = k / TX + HY;
+        c = k % TX + 2;
+        return;
+    }
+    int m = k - NT;
+    if (m < HY * AX) {
+        r = m / AX;
+        c = m - r * AX;
+        return;
+    }
+    m -= HY * AX;
+    if (m < HY * AX) {
+        const int q = m / AX;
+        r = AY - HY + q;
+        c = m - q * AX;
+        return;
+    }
+    m -= HY * AX;
+    const int e = m & 3;
+    r = HY + (m >> 2);
+    c = e < 2 ? e : AX - 4 + e;
 }
 
 // Per-tile constants of one CTA's work: the column tile at (x0, y0) over the
@@ -230,11 +377,12 @@ __device__ __forceinline__ TileF tile_setup(const GeoF &g, int bx, int by, int b
 // of P - P0 and (u, 1/rho) of the interior nodes; thread tid of NT. Each
 // thread owns up to KA halo nodes and issues all their loads before any
 // arithmetic, for memory-level parallelism.
-template <int LAT, bool MASK, typename ST, typename SM>
+template <int LAT, bool MASK, bool TM = false, bool E64 = false, typename ST, typename SM>
 __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
                                         const uint8_t *__restrict__ mask,
                                         const ST *__restrict__ f, SM &sm, const TileF &T,
-                                        int pl, int tid, const float *__restrict__ rho_src)
+                                        int pl, int tid, const float *__restrict__ rho_src,
+                                        unsigned tbase = 0)
 {
     constexpr bool SHIFT = IsShifted<ST>::value;
     using L = LatF<LAT>;
@@ -262,8 +410,8 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
     for (int u = 0; u < KA; ++u) {
         const int k = tid + u * NT;
         live[u] = k < AX * AY;
-        const int kk = live[u] ? k : 0;
-        const int r = kk / AX, c = kk - r * AX;
+        int r, c;
+        halo_rc<LAT>(live[u] ? k : 0, r, c);
         nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
         solid[u] = MASK && live[u] && mask[nk[u]];
         if (live[u] && !solid[u]) {
@@ -274,10 +422,10 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
 #pragma unroll
     for (int u = 0; u < KA; ++u) {
         if (!live[u]) continue;
-        const int k = tid + u * NT;
-        const int r = k / AX, c = k - r * AX;
+        int r, c;
+        halo_rc<LAT>(tid + u * NT, r, c);
         const bool ring1 = c >= 1 && c < AX - 1 && (!THREE || (r >= 1 && r < AY - 1));
-        float rho, d, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+        float rho, d, psi64 = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
         float4 uvk = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (solid[u]) {
             rho = p.rho_w;
@@ -311,9 +459,15 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
                 gz = rho * uz * uz * uz;
                 uvk = make_float4(ux, uy, uz, inv);
             }
-            d = excess_pressure_f(p, rho);
+            if constexpr (E64) {
+                const double dd = excess_pressure_d(p, (double)rho);
+                d = (float)dd;
+                psi64 = (float)sqrt(fabs(dd));
+            } else {
+                d = excess_pressure_f(p, rho);
+            }
         }
-        s_rp[rs][r][c] = f2(rho, sqrtf(fabsf(d)));
+        s_rp[rs][r][c] = f2(rho, E64 && !solid[u] ? psi64 : sqrtf(fabsf(d)));
         if (ring1) {
             const int gr = THREE ? r - 1 : 0;
             s_g[gs][0][gr][c - 1] = gx;
@@ -326,6 +480,11 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
             sm.uv[pl & 3][ir][ic] = uvk;
         }
     }
+    // the thread's interior node (its halo node tid), for phase B two planes on
+    if constexpr (TM) {
+        __syncwarp();   // tcgen05.st is warp-collective: reconverge after the loops
+        tmem_store_pop<Q>(tmem_slot<LAT>(tbase, pl % 3), fi[0]);
+    }
 }
 
 // Phase B of iteration pl >= 4: the tile's nodes on plane zc = z0 + pl - 4
@@ -333,12 +492,13 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
 // their post-collision populations with halfway bounce-back; thread tid of
 // NT owns node (tid % TX, tid / TX), which the caller has checked to lie in
 // the lattice (a ragged tile's last columns or rows may not).
-template <int LAT, bool MASK, typename ST, typename SM>
+template <int LAT, bool MASK, bool TM = false, bool E64 = false, typename ST, typename SM>
 __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
                                         const uint8_t *__restrict__ mask,
                                         const ST *__restrict__ f, ST *__restrict__ fout,
                                         int *__restrict__ status, SM &sm, const TileF &T, int pl,
-                                        int tid, float *__restrict__ rho_dst)
+                                        int tid, float *__restrict__ rho_dst, unsigned tbase = 0,
+                                        bool inside = true)
 {
     constexpr bool SHIFT = IsShifted<ST>::value;
     using L = LatF<LAT>;
@@ -356,11 +516,19 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
     const int pc = pl - 2;             // ring index of the collided plane
     const int zc = z0 + pl - 4;
     const unsigned n = (unsigned)xi + (unsigned)g.nx * (unsigned)yi + plane * (unsigned)zc;
+    // the node's own populations: from Tensor Memory, where phase A left them
+    // (all lanes of the warp take part), or read again (an L2 hit), first
+    float fi[Q];
+    if constexpr (TM) {
+        __syncwarp();   // tcgen05.ld is warp-collective
+        tmem_load_pop<Q>(tmem_slot<LAT>(tbase, pc % 3), fi);
+        if (!inside) return;
+    }
     if (!(MASK && mask[n])) {
-        // the node's own populations (second read, an L2 hit), issued first
-        float fi[Q];
+        if constexpr (!TM) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
+            for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
+        }
         const int cr = ty + HY, cc = tx + 2;
         const float2 c0 = s_rp[pc % RS][cr][cc];
         const float rho = c0.x;
@@ -373,6 +541,45 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
         int slot[5];
 #pragma unroll
         for (int dz = 0; dz < 5; ++dz) slot[dz] = (pc - 2 + dz) % RS;
+        float F[3];
+        if constexpr (E64) {
+            // the same sums in FP64: neighbours widened, sums and force in FP64
+            double Sp[3] = {0.0, 0.0, 0.0}, Sr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int s = 1; s <= 2; ++s) {
+                double Pp[3][3], Pr[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) Pp[a][k] = Pr[a][k] = 0.0;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+                    if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
+                    const float2 r2 = s_rp[slot[2 + s * c[2]]][cr + s * c[1]][cc + s * c[0]];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (c[a] == 0) continue;
+                        const int k = (a != 0 && c[0] != 0) + (a != 1 && c[1] != 0) +
+                                      (a != 2 && c[2] != 0);
+                        Pp[a][k] += c[a] * (double)r2.y;
+                        Pr[a][k] += c[a] * (double)r2.x;
+                    }
+                }
+                const double gp = s == 1 ? 4.0 / 3.0 : -1.0 / 6.0, gr = s == 1 ? 2.0 : -1.0;
+                const double w0 = THREE ? 2.0 / 9.0 : 1.0 / 3.0, w1 = THREE ? 1.0 / 18.0 : 1.0 / 12.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (!THREE && a == 1) continue;
+                    Sp[a] += gp * (w0 * Pp[a][0] + w1 * Pp[a][1] + (THREE ? Pp[a][2] / 72.0 : 0.0));
+                    Sr[a] += gr * (w0 * Pr[a][0] + w1 * Pr[a][1] + (THREE ? Pr[a][2] / 72.0 : 0.0));
+                }
+            }
+            const double rd = rho, sd = (double)s_sg[pc % RS][ty][tx] * (double)c0.y;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                F[a] = (float)(rd * (double)p.g[a] - 2.0 * sd * Sp[a] - p.dkappa * rd * Sr[a]);
+        } else {
         float2 S[3] = {f2(0.0f, 0.0f), f2(0.0f, 0.0f), f2(0.0f, 0.0f)};   // (S_psi, S_rho)
         const float2 neg1 = f2(-1.0f, -1.0f);
 #pragma unroll
@@ -418,10 +625,10 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
                 S[a] = __ffma2_rn(Dw, gsr, S[a]);
             }
         }
-        float F[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)   // Korteweg force plus the body force rho g
             F[a] = __fmaf_rn(rho, p.g[a], -2.0f * spsi * S[a].x - p.kappa * rho * S[a].y);
+        }
         // Phi_aa = -(1 - omega/2) (g_a(r + e_a) - g_a(r - e_a)) / 2, the node's omega
         const float om = p.var_visc ? omega_var_f(p, rho) : p.omega;
         const float pref = p.var_visc ? p.phi_sign * (1.0f - 0.5f * om) : p.phi_pref;
@@ -483,13 +690,15 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
 // One CTA's work: the column tile (bx, by) over the plane chunk bz. Six
 // (rho, |psi|) slots and five rho u^3 slots let the next plane enter while
 // slower warps still collide: one barrier per plane.
-template <int LAT, bool MASK, typename ST = float, typename SM = SharedF<LAT>>
+template <int LAT, bool MASK, typename ST = float, typename SM = SharedF<LAT>, bool TM = false,
+          bool E64 = false>
 __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                                            const uint8_t *__restrict__ mask,
                                            const ST *__restrict__ f, ST *__restrict__ fout,
                                            int *__restrict__ status, int bx, int by, int bz,
                                            SM &sm, const float *__restrict__ rho_src = nullptr,
-                                           float *__restrict__ rho_dst = nullptr)
+                                           float *__restrict__ rho_dst = nullptr,
+                                           unsigned tbase = 0)
 {
     static_assert(!(IsShifted<ST>::value && MASK), "shifted storage runs lattices without solid nodes");
     constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
@@ -498,9 +707,10 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
     const bool inside = T.x0 + tid % TX < g.nx && T.y0 + tid / TX < g.ny;
     __syncthreads();
     for (int pl = 0; pl < T.np; ++pl) {
-        phase_a<LAT, MASK>(g, p, mask, f, sm, T, pl, tid, rho_src);
+        phase_a<LAT, MASK, TM, E64>(g, p, mask, f, sm, T, pl, tid, rho_src, tbase);
         __syncthreads();
-        if (pl >= 4 && inside) phase_b<LAT, MASK>(g, p, mask, f, fout, status, sm, T, pl, tid, rho_dst);
+        if (TM ? pl >= 4 : pl >= 4 && inside)
+            phase_b<LAT, MASK, TM, E64>(g, p, mask, f, fout, status, sm, T, pl, tid, rho_dst, tbase, inside);
     }
 }
 
@@ -527,11 +737,6 @@ constexpr long long kWaitCycles = 2000000000ll;
 template <int LAT> struct SharedWS : SharedF<LAT> {
     unsigned long long full[6], empty[6];
 };
-
-__device__ __forceinline__ unsigned smem_u32(const void *ptr)
-{
-    return (unsigned)__cvta_generic_to_shared(ptr);
-}
 
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
@@ -618,20 +823,47 @@ k_step_f32_ws(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__
 }
 
 // FP32 populations; dynamic shared memory of sizeof(SharedF<LAT>).
-template <int LAT, bool MASK>
+// E64: the EOS, pseudo-potential and force sums in FP64 (LBM_FLAG_EOS_F64).
+template <int LAT, bool MASK, bool E64 = false>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
 k_step_f32(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
            float *__restrict__ fout, int *__restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SharedF<LAT> &sm = *reinterpret_cast<SharedF<LAT> *>(smem_raw);
-    fused_tile<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+    fused_tile<LAT, MASK, float, SharedF<LAT>, false, E64>(g, p, mask, f, fout, status, blockIdx.x,
+                                                           blockIdx.y, blockIdx.z, sm);
+}
+
+// FP32 populations with the interior nodes' populations kept in Tensor
+// Memory between the phases (TmemF::COLS columns per block, allocated by
+// warp 0 and freed before the block exits); dynamic shared memory of
+// sizeof(SharedF<LAT>).
+template <int LAT, bool MASK>
+__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
+k_step_f32_tm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
+              float *__restrict__ fout, int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedF<LAT> &sm = *reinterpret_cast<SharedF<LAT> *>(smem_raw);
+    constexpr unsigned COLS = TmemF<LAT>::COLS;
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned tbase = sm.tmem;
+    fused_tile<LAT, MASK, float, SharedF<LAT>, true>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y,
+                                                     blockIdx.z, sm, nullptr, nullptr, tbase);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, COLS);
 }
 
 // Shifted 16-bit storage (ST = __half or __nv_bfloat16): populations h_i
 // with the source densities rho_src read and rho_dst written; dynamic shared
 // memory of sizeof(SharedS<LAT>).
-template <int LAT, typename ST>
+template <int LAT, typename ST, bool E64 = false>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
 k_step_shifted(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
                const float *__restrict__ rho_src, float *__restrict__ rho_dst,
@@ -639,8 +871,8 @@ k_step_shifted(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
-    fused_tile<LAT, false, ST, SharedS<LAT>>(g, p, nullptr, f, fout, status, blockIdx.x, blockIdx.y,
-                                            blockIdx.z, sm, rho_src, rho_dst);
+    fused_tile<LAT, false, ST, SharedS<LAT>, false, E64>(g, p, nullptr, f, fout, status, blockIdx.x,
+                                                         blockIdx.y, blockIdx.z, sm, rho_src, rho_dst);
 }
 
 // Many lattices of one type and one storage in one launch: descriptor of one

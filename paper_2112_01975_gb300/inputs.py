@@ -88,19 +88,20 @@ def add_noise(rho: np.ndarray, rel: float, seed: int) -> np.ndarray:
 
 
 def pillar_mask(nx: int, ny: int, nz: int, side: int = 8, height: int = 16,
-                pitch: int = 16, seed: int = 4) -> np.ndarray:
-    """uint8 solid mask: wall at z = 0 plus square pillars (side x side x
-    height) on a square lattice of the given pitch, on z = 1..height. The
-    pillar lattice offset in x and y comes from the seed."""
+                pitch: int = 16, seed: int = 4, wall: int = 1) -> np.ndarray:
+    """uint8 solid mask: a wall of `wall` planes (z < wall) plus square
+    pillars (side x side x height) on a square lattice of the given pitch, on
+    z = wall .. wall + height - 1. The pillar lattice offset in x and y comes
+    from the seed."""
     off = splitmix64(np.array([seed], dtype=np.uint64))[0]
     ox = int(off % np.uint64(pitch))
     oy = int((off >> np.uint64(32)) % np.uint64(pitch))
     m = np.zeros((nz, ny, nx), dtype=np.uint8)
-    m[0] = 1
+    m[:wall] = 1
     xs = ((np.arange(nx) - ox) % pitch) < side
     ys = ((np.arange(ny) - oy) % pitch) < side
     col = np.logical_and(ys[:, None], xs[None, :])
-    m[1:1 + height][:, col] = 1
+    m[wall:wall + height][:, col] = 1
     return m.ravel()
 
 
@@ -145,6 +146,7 @@ class Workload:
     gap: float = 8.0
     u_down: float = 0.0
     pillar: tuple = (8, 16, 16)   # side, height, pitch
+    wall: int = 1                 # planes of the wall under the pillars
 
     @property
     def nodes(self) -> int:
@@ -167,8 +169,8 @@ class Workload:
         if self.mask_seed is not None:
             side, height, pitch = self.pillar
             mask = pillar_mask(nx, ny, nz, side=side, height=height, pitch=pitch,
-                               seed=self.mask_seed)
-            c = (nx // 2, ny // 2, height + R + self.gap)
+                               seed=self.mask_seed, wall=self.wall)
+            c = (nx // 2, ny // 2, self.wall + height - 1 + R + self.gap)
             r = drop(nx, ny, nz, R, self.rho_v, self.rho_l, center=c)
         elif self.centres:
             r = drops(nx, ny, nz, [tuple(v * s for v in cc) for cc in self.centres], R,
@@ -236,18 +238,21 @@ COALESCENCE_D3Q27_256 = Workload("d3q27_coalescence_256^3_pr_tr0.45", 1, 256, 25
                                  radius=40.0, seed=3, a=0.00162040657246882, b=2.0 / 21.0,
                                  steps=10000, centres=((88.0, 128.0, 128.0), (168.0, 128.0, 128.0)))
 
-# D3Q27 drop impact on a textured wall, 384x384x256: wall at z = 0 plus
+# D3Q27 drop impact on a textured wall, 384x384x256: a wall two planes thick
+# (z = 0, 1: the force stencils reach two nodes, so a thinner wall would
+# couple the fluid above it to the fluid below its periodic image) plus
 # 8x8x16 square pillars at pitch 16 (lattice offset from seed 4), solid
 # density rho_w = rho_v (non-wetting); Peng-Robinson (b = 2/21, a scaled for
 # a liquid dP/drho of 0.1) at T/Tc = 0.5 (Maxwell density ratio 1.1e4); a
 # drop of radius 60 whose lowest point is 8 nodes above the pillar tops,
-# moving down at U = 0.05 in the liquid (We = rho_l U^2 2R / sigma = 19),
-# tau = 0.725, no noise. The largest single-GPU workload; FP32 storage.
+# moving down at U = 0.115 in the liquid (We = rho_l U^2 2R / sigma = 100,
+# sigma = 0.146), tau = 0.725 (Re = U 2R / nu = 184), no noise. The largest
+# single-GPU workload; FP32 storage.
 IMPACT_D3Q27_384 = Workload("d3q27_impact_384x384x256_pr_tr0.5", 1, 384, 384, 256, 1, 0.5,
                             kappa=0.011670519231996029, tau=0.725,
                             rho_v=0.000832893711960915, rho_l=9.219284708837831,
                             radius=60.0, seed=4, a=0.00216512412385399, b=2.0 / 21.0,
-                            noise=0.0, steps=20000, mask_seed=4, u_down=0.05)
+                            noise=0.0, steps=20000, mask_seed=4, u_down=0.115, wall=2)
 
 WORKLOADS = {w.name: w for w in (DROP_D2Q9_64, DROP_D3Q27_128, DROP_D3Q27_96,
                                  COALESCENCE_D3Q27_256, IMPACT_D3Q27_384)}

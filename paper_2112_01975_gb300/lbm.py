@@ -18,7 +18,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 D2Q9, D3Q27 = 0, 1
 EOS_VDW, EOS_PR, EOS_RKS, EOS_CS, EOS_SC1, EOS_SC2 = 0, 1, 2, 3, 4, 5
 F64, F32, F16S, BF16S = 0, 1, 2, 3
+FUSED_PLAIN, FUSED_WARP_SPECIALISED, FUSED_TMEM = 0, 1, 2
+FUSED_NAMES = {0: "plain", 1: "warp-specialised", 2: "tensor-memory"}
 FLAG_PHI_OFF = 1
+FLAG_EOS_F64 = 2
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
           5: "LBM_ETIMEOUT", 6: "LBM_ESTATE", 7: "LBM_ETOOBIG"}
 
@@ -64,8 +67,8 @@ def _load():
     L.lbm_autotune.argtypes = [vp, C.POINTER(C.c_int)]
     L.lbm_get_tile.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lbm_set_tile.argtypes = [vp, C.c_int]
-    L.lbm_set_warp_specialized.argtypes = [vp, C.c_int]
-    L.lbm_get_warp_specialized.argtypes = [vp, C.POINTER(C.c_int)]
+    L.lbm_set_fused_variant.argtypes = [vp, C.c_int]
+    L.lbm_get_fused_variant.argtypes = [vp, C.POINTER(C.c_int)]
     L.lbm_reduce_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.lbm_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
     L.lbm_batch_step.argtypes = [vp, i64]
@@ -101,8 +104,8 @@ lbm_set_chunk = _lib.lbm_set_chunk
 lbm_autotune = _lib.lbm_autotune
 lbm_get_tile = _lib.lbm_get_tile
 lbm_set_tile = _lib.lbm_set_tile
-lbm_set_warp_specialized = _lib.lbm_set_warp_specialized
-lbm_get_warp_specialized = _lib.lbm_get_warp_specialized
+lbm_set_fused_variant = _lib.lbm_set_fused_variant
+lbm_get_fused_variant = _lib.lbm_get_fused_variant
 lbm_reduce_noalloc = _lib.lbm_reduce_noalloc
 lbm_batch_create = _lib.lbm_batch_create
 lbm_batch_step = _lib.lbm_batch_step
@@ -286,9 +289,10 @@ class LBM:
         self._check(_lib.lbm_set_chunk(self._h, int(chunk)))
 
     def autotune(self) -> int:
-        """Time the fused step's chunk candidates (and, for D3Q27 FP32, the 8-
-        and 7-row tiles) on the current state (which is restored) and keep the
-        fastest; returns the chunk (0 for FP64)."""
+        """Time the fused step's chunk candidates (and, for FP32, its three
+        forms and, for D3Q27, the 8- and 7-row tiles) on the current state
+        (which is restored) and keep the fastest; returns the chunk (0 for
+        FP64)."""
         c = C.c_int()
         self._check(_lib.lbm_autotune(self._h, C.byref(c)))
         return c.value
@@ -297,15 +301,16 @@ class LBM:
         """Tile height of the D3Q27 FP32 step: 8 (default) or 7 rows."""
         self._check(_lib.lbm_set_tile(self._h, int(tile_y)))
 
-    def set_warp_specialized(self, on: bool):
-        """Warp-specialised (True) or plain (False) FP32 fused step."""
-        self._check(_lib.lbm_set_warp_specialized(self._h, int(bool(on))))
+    def set_fused_variant(self, variant: int):
+        """Form of the FP32 fused step: FUSED_PLAIN, FUSED_WARP_SPECIALISED
+        or FUSED_TMEM (bitwise the same results)."""
+        self._check(_lib.lbm_set_fused_variant(self._h, int(variant)))
 
     @property
-    def warp_specialized(self) -> bool:
+    def fused_variant(self) -> int:
         v = C.c_int()
-        self._check(_lib.lbm_get_warp_specialized(self._h, C.byref(v)))
-        return bool(v.value)
+        self._check(_lib.lbm_get_fused_variant(self._h, C.byref(v)))
+        return v.value
 
     def tile(self):
         """(tile_x, tile_y) of the fused step in use; (0, 0) for FP64."""

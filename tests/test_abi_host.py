@@ -93,8 +93,8 @@ def test_null_handle_calls_are_errors(lib):
     assert lib.lbm_get_tile(None, C.byref(x), C.byref(y)) == 1 and x.value == -1
     assert lib.lbm_set_tile(None, 7) == 1
     on = C.c_int(-1)
-    assert lib.lbm_set_warp_specialized(None, 1) == 1
-    assert lib.lbm_get_warp_specialized(None, C.byref(on)) == 1 and on.value == -1
+    assert lib.lbm_set_fused_variant(None, 1) == 1
+    assert lib.lbm_get_fused_variant(None, C.byref(on)) == 1 and on.value == -1
     lib.lbm_last_error.restype = C.c_char_p
     assert lib.lbm_last_error(None) == b"null handle"
     lib.lbm_destroy(None)

@@ -1,0 +1,61 @@
+"""The FP64-EOS form of the reduced-precision steps (LBM_FLAG_EOS_F64: the
+EOS, psi and the force's stencil sums in FP64 inside the fused step, the
+populations FP32 or 16-bit shifted) against the FP64 oracle at a
+deep-subcritical state: a Peng-Robinson T/Tc 0.45 slab (Maxwell density
+ratio 6.6e4, width 5, tau 0.725), node by node at each storage's tolerance
+(0.5 % FP32, 2 % 16-bit shifted), with the plain FP32-EOS form beside it."""
+import numpy as np
+import pytest
+
+from oracle.lbm import OracleLBM
+from paper_2112_01975_gb300 import eos_tables, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_01975_gb300 import build
+    build.build()
+    from paper_2112_01975_gb300 import lbm as L
+    tr = 0.45
+    a = eos_tables.stable_a(1, tr)
+    rv, rl, _ = eos_tables.coexistence(1, tr, a)
+    kap = eos_tables.kappa_for_width(1, tr, a, width=5.0)
+    nx, steps = 128, 2000
+    rho = inputs.add_noise(inputs.slab(nx, 5, 1, 32, 96, rv, rl, 5.0), 1e-4, 13)
+    o = OracleLBM(0, nx, 5, 1, 1, tr, kap, 0.725, a=a)
+    o.init(rho)
+    o.step(steps)
+    return L, dict(tr=tr, a=a, rv=rv, rl=rl, kap=kap, nx=nx, steps=steps, rho=rho), o.moments()[0]
+
+
+def _run(L, c, storage, flags):
+    g = L.LBM(0, c["nx"], 5, 1, 1, c["tr"], c["kap"], 0.725, a=c["a"], storage=storage, flags=flags)
+    g.init(c["rho"])
+    g.step(c["steps"])
+    return g
+
+
+@pytest.mark.parametrize("storage,tol", [(1, 5e-3), (2, 2e-2), (3, 2e-2)])
+def test_eos64_against_the_oracle(env, storage, tol):
+    L, c, ro = env
+    g = _run(L, c, storage, L.FLAG_EOS_F64)
+    rg = g.moments()[0]
+    err64 = float(np.max(np.abs(rg - ro) / ro))
+    assert err64 < tol, err64
+    rp = _run(L, c, storage, 0).moments()[0]
+    err32 = float(np.max(np.abs(rp - ro) / ro))
+    print(f"storage {storage}: max rel density error FP64-EOS {err64:.2e}, FP32-EOS {err32:.2e}")
+
+
+def test_eos64_refuses_other_forms_and_batches(env):
+    L, c, _ = env
+    g = _run(L, c, 1, L.FLAG_EOS_F64)
+    with pytest.raises(L.LBMError):
+        g.set_fused_variant(L.FUSED_TMEM)
+    with pytest.raises(L.LBMError):
+        L.Batch([g])

@@ -259,3 +259,42 @@ def test_f32_autotune_keeps_the_state(lbm):
     assert np.array_equal(g.get_populations(), f0)
     g.step(6)
     g.sync()
+
+
+@pytest.fixture(scope="module")
+def pillar_oracle():
+    """The 32^3 pillar case on the oracle, 1000 steps (once for the module)."""
+    from test_gpu_parity import _pillar_case
+    w, n, mask, rho = _pillar_case()
+    kw = dict(mask=mask, a=w.a, b=w.b, rho_w=w.rho_v)
+    try:   # the -fopenmp build: bitwise the plain oracle, on all host cores
+        o = OracleLBM(1, n, n, n, w.eos, w.t_over_tc, w.kappa, 0.8, openmp=True, **kw)
+    except Exception:
+        o = OracleLBM(1, n, n, n, w.eos, w.t_over_tc, w.kappa, 0.8, **kw)
+    o.init(rho)
+    o.step(1000)
+    return w, n, mask, rho, o
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_f32_pr_pillars_32cubed_1000_steps(lbm, pillar_oracle, variant):
+    """The 32^3 pillar case of the FP64 parity tests (a wall with 4x4x6
+    pillars, a Peng-Robinson drop above them) in FP32 storage, with each form
+    of the fused step (plain, warp-specialised, Tensor Memory), against the
+    FP64 oracle after 1000 steps at the FP32 tolerances; the three forms
+    agree bitwise."""
+    w, n, mask, rho, o = pillar_oracle
+
+    def run(var):
+        g = lbm.LBM(1, n, n, n, w.eos, w.t_over_tc, w.kappa, 0.8, mask=mask, a=w.a, b=w.b,
+                    rho_w=w.rho_v, storage=lbm.F32)
+        g.set_fused_variant(var)
+        g.init(rho)
+        g.step(1000)
+        return g
+
+    g = run(variant)
+    er, eu, eU = errs(g, o, mask)
+    assert er < RHO_TOL and eu < U_TOL and eU < U_TOL, (er, eu, eU)
+    if variant:
+        assert np.array_equal(run(0).get_populations(), g.get_populations())

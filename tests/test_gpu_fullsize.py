@@ -12,10 +12,10 @@ nodes next to a solid).
 
 Workloads: two touching drops of radius 40 in a periodic 256^3 box at
 Peng-Robinson T/Tc = 0.45 (coalescence, density ratio 6.6e4); a drop of
-radius 60 moving down at U = 0.05 (We = rho_l U^2 D / sigma = 19) onto a
-wall with 8x8x16 pillars at pitch 16 in a 384x384x256 box at T/Tc = 0.5
-(impact, density ratio 1.1e4). Both at nu = 0.075 (tau = 0.725), interface
-width 5, started at rest in the physical velocity.
+radius 60 moving down at U = 0.115 (We = rho_l U^2 D / sigma = 100) onto a
+two-plane wall with 8x8x16 pillars at pitch 16 in a 384x384x256 box at
+T/Tc = 0.5 (impact, density ratio 1.1e4). Both at nu = 0.075 (tau = 0.725),
+interface width 5, started at rest in the physical velocity.
 """
 import numpy as np
 import pytest
@@ -131,27 +131,30 @@ def test_coalescence_256cubed(env, storage):
 
 
 def test_impact_on_pillars_384x384x256(env):
+    """The impact workload (inputs.IMPACT_D3Q27_384: a two-plane wall with
+    8x8x16 pillars, a drop of radius 60 at We = 100) in FP32 for 300 steps:
+    mass, bounds, contact with the pillar tops, sampled nodes against the
+    oracle's node-local update."""
     torch, L = env
-    nx, ny, nz, R, tr, U = 384, 384, 256, 60.0, 0.5, 0.05
-    a, rv, rl, kap = pr_state(tr)
+    w = inputs.IMPACT_D3Q27_384
+    nx, ny, nz = w.nx, w.ny, w.nz
     shape = (nz, ny, nx)
-    mask = inputs.pillar_mask(nx, ny, nz, seed=4)
-    drop = inputs.drop(nx, ny, nz, R, rv, rl, width=W, center=(nx // 2, ny // 2, 16 + R + 8))
-    u0 = np.zeros(3 * drop.size)
-    u0[2 * drop.size:] = np.where(mask == 1, 0.0, -U * (drop - rv) / (rl - rv))
-    rho = np.where(mask == 1, rv, drop)
-    g = L.LBM(1, nx, ny, nz, 1, tr, kap, TAU, mask=mask, a=a, rho_w=rv, storage=L.F32)
+    rho, u0, mask = w.fields()
+    rv, rl = w.rho_v, w.rho_l
+    g = L.LBM(1, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, w.tau, mask=mask, a=w.a, b=w.b,
+              rho_w=w.rho_w, storage=L.F32)
     g.init(rho, u0)
     m0, _ = g.reduce()
-    g.step(400)      # the drop's front reaches the pillar tops after ~160 steps
+    g.step(300)      # the drop's front reaches the pillar tops after ~70 steps
     m1, _ = g.reduce()
     assert abs(m1 / m0 - 1) < MASS_TOL[1]
     rho_now = g.moments()[0]
     assert rho_now[mask == 0].min() > 0.02 * rv and rho_now.max() < 1.1 * rl
-    # liquid between the pillars' tops and the drop: contact has been made
-    top = rho_now.reshape(nz, ny, nx)[17, ny // 2 - 16:ny // 2 + 16, nx // 2 - 16:nx // 2 + 16]
+    # liquid on the plane just above the pillar tops, under the drop: contact
+    zt = w.wall + w.pillar[1]
+    top = rho_now.reshape(nz, ny, nx)[zt, ny // 2 - 16:ny // 2 + 16, nx // 2 - 16:nx // 2 + 16]
     assert top.max() > 0.5 * rl
-    o = OracleLBM(1, 5, 5, 5, 1, tr, kap, TAU, a=a, rho_w=rv)
+    o = OracleLBM(1, 5, 5, 5, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b, rho_w=w.rho_w)
     check_sampled_step(torch, g, o, shape, mask, samples(shape, rho_now, mask, 4), STEP_TOL[1])
     g.sync()
     g.close()

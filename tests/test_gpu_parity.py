@@ -91,6 +91,39 @@ def test_d3q27_pr_mask_ragged_1000_steps(lbm):
     assert er < TOL and eu < TOL and eU < TOL, (er, eu, eU)
 
 
+def _pillar_case():
+    """D3Q27 32^3, Peng-Robinson T/Tc 0.7: a wall at z = 0 with 4x4x6
+    pillars at pitch 8 (seeded offset), solid density rho_v, and a drop of
+    radius 7 resting 3 nodes above the pillar tops (seeded noise)."""
+    w = inputs.DROP_D3Q27_128
+    n = 32
+    mask = inputs.pillar_mask(n, n, n, side=4, height=6, pitch=8, seed=4)
+    rho = inputs.add_noise(inputs.drop(n, n, n, 7.0, w.rho_v, w.rho_l, center=(16, 16, 16)), 1e-4, 23)
+    return w, n, mask, np.where(mask == 1, w.rho_v, rho)
+
+
+def test_d3q27_pr_pillars_32cubed_1000_steps(lbm):
+    """The 32^3 pillar case in FP64 against the oracle after 1000 steps at
+    1e-10, with mass conserved to 1e-13."""
+    w, n, mask, rho = _pillar_case()
+    g = lbm.LBM(1, n, n, n, w.eos, w.t_over_tc, w.kappa, 0.8, mask=mask, a=w.a, b=w.b, rho_w=w.rho_v)
+    try:   # the -fopenmp build: bitwise the plain oracle, on all host cores
+        o = OracleLBM(1, n, n, n, w.eos, w.t_over_tc, w.kappa, 0.8, mask=mask, a=w.a, b=w.b,
+                      rho_w=w.rho_v, openmp=True)
+    except Exception:
+        o = OracleLBM(1, n, n, n, w.eos, w.t_over_tc, w.kappa, 0.8, mask=mask, a=w.a, b=w.b,
+                      rho_w=w.rho_v)
+    g.init(rho)
+    o.init(rho)
+    m0, _ = g.reduce()
+    g.step(1000)
+    o.step(1000)
+    er, eu, eU = compare(g, o, mask)
+    assert er < TOL and eu < TOL and eU < TOL, (er, eu, eU)
+    m1, _ = g.reduce()
+    assert abs(m1 / m0 - 1) < 1e-13
+
+
 def test_d3q27_vdw_drop_odd_sizes_1000_steps(lbm):
     w = inputs.DROP_D2Q9_64
     nx, ny, nz = 21, 19, 17
