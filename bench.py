@@ -90,9 +90,10 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 7, 8],
                     help="D3Q27 FP32 tile height (0: picked by the autotuner, or 8 with --chunk)")
-    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2],
-                    help="FP32 fused-step form: 0 plain, 1 warp-specialised, 2 Tensor Memory "
-                         "(-1: picked by the autotuner, or plain with --chunk)")
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="fused-step form: 0 plain, 1 warp-specialised, 2 Tensor Memory, 3 "
+                         "warp-specialised with Tensor Memory (-1: picked by the autotuner, "
+                         "or plain with --chunk)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--eos64", action="store_true",
@@ -571,7 +572,7 @@ def main():
     alg = ALG_BYTES_PER_LU[(w.lattice, args.storage)] * nodes
     per_step = launches / args.steps if args.steps else 1
     tile = g.tile()
-    variant = g.fused_variant if storage == F32 else 0
+    variant = g.fused_variant if storage != F64 else 0
     if storage != F64:
         ms_launch = ms / max(launches, 1)
         achieved = alg / (ms_launch * 1e-3) / 1e9
@@ -581,8 +582,11 @@ def main():
                     "frac_of_nominal_7900_gbs": achieved / 7900.0,
                     "kernel": {0: "k_step_f32 (fused step)",
                                1: "k_step_f32_ws (fused step, warp-specialised)",
-                               2: "k_step_f32_tm (fused step, Tensor Memory staging)"}[variant]
-                    if storage == F32 else "k_step_shifted",
+                               2: "k_step_f32_tm (fused step, Tensor Memory staging)",
+                               3: "k_step_f32_wstm (fused step, warp-specialised, Tensor Memory "
+                                  "staging)"}[variant]
+                    if storage == F32 else
+                    ("k_step_shifted_tm" if variant == 2 else "k_step_shifted"),
                     "peak_source": peak_kind + " hbm_gbs (burst copy)",
                     "alg_bytes_per_launch": alg, "ms_per_launch": ms_launch,
                     "ms_per_launch_source": "CUDA events over the timed graph replays / launches",

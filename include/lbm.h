@@ -277,8 +277,9 @@ int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y);
  * storage. */
 int lbm_set_tile(lbm_handle h, int tile_y);
 
-/* Forms of the LBM_F32 fused step; the same arithmetic in the same order,
- * so results are bitwise the same whichever runs.
+/* Forms of the fused step of the reduced storages (LBM_F32; LBM_F16S and
+ * LBM_BF16S have the plain and the Tensor Memory form); the same arithmetic
+ * in the same order, so results are bitwise the same whichever runs.
  *   LBM_FUSED_PLAIN (default): one thread group per tile; each entering
  *     plane's densities, pseudo-potentials and velocities are formed, the
  *     block synchronises, and the plane two behind collides and streams,
@@ -293,11 +294,16 @@ int lbm_set_tile(lbm_handle h, int tile_y);
  *     SM's Tensor Memory from the plane's entry to its collision instead of
  *     being read twice; each block holds 256 columns (D3Q27; 64 for D2Q9) of
  *     Tensor Memory while it runs. */
-enum { LBM_FUSED_PLAIN = 0, LBM_FUSED_WARP_SPECIALISED = 1, LBM_FUSED_TMEM = 2 };
+enum { LBM_FUSED_PLAIN = 0, LBM_FUSED_WARP_SPECIALISED = 1, LBM_FUSED_TMEM = 2, LBM_FUSED_WS_TMEM = 3 };
 
-/* Select a form of the LBM_F32 fused step (lbm_autotune times all three).
- * LBM_EINVAL for an unknown form, or a form other than LBM_FUSED_PLAIN with
- * another storage. */
+/*   LBM_FUSED_WS_TMEM (D3Q27 FP32, 32 x 8 tiles): the warp-specialised form
+ *     with the Tensor Memory staging, the producer that loads a node leaving
+ *     its populations in the lane of the consumer that collides it.
+ * Select a form of the fused step (lbm_autotune times the forms the
+ * storage has). LBM_EINVAL for an unknown form, a form other than
+ * LBM_FUSED_PLAIN with LBM_F64 storage or LBM_FLAG_EOS_F64, or the
+ * warp-specialised forms with shifted storage, or LBM_FUSED_WS_TMEM with D2Q9
+ * or 7-row tiles. */
 int lbm_set_fused_variant(lbm_handle h, int variant);
 
 /* *variant = the form of the fused step in use. */

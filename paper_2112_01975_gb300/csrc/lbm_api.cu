@@ -33,7 +33,7 @@ struct lbm_ctx {
     bool e64 = false;    // reduced storage: EOS, psi and force sums in FP64 (LBM_FLAG_EOS_F64)
     int storage, flags;
     double t_over_tc, tau;
-    std::vector<uint8_t> mask_host;
+    std::vector<uint8_t> mask_host, zsolid_host;
     bool any_solid = false;
     int device;
     cudaStream_t own_stream = nullptr, stream = nullptr, cap_stream = nullptr;
@@ -83,7 +83,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, rs0, rs1, rp, u, g, mask, partial, sums, status, total;
+    size_t f0, f1, rs0, rs1, rp, u, g, mask, zs, partial, sums, status, total;
 };
 
 bool shifted(int storage) { return storage == LBM_F16S || storage == LBM_BF16S; }
@@ -93,7 +93,8 @@ size_t pop_bytes(int storage)
     return storage == LBM_F64 ? sizeof(double) : storage == LBM_F32 ? sizeof(float) : 2;
 }
 
-Layout layout_for(int D, int Q, size_t N, int storage)
+// planes: the fused step's march-axis extent (nz; ny for D2Q9).
+Layout layout_for(int D, int Q, size_t N, int storage, size_t planes)
 {
     Layout L;
     size_t o = 0;
@@ -111,6 +112,7 @@ Layout layout_for(int D, int Q, size_t N, int storage)
     L.u = o; o = align_up(o + sizeof(double) * D * N);
     L.g = o; o = align_up(o + sizeof(double) * D * N);
     L.mask = o; o = align_up(o + N);
+    L.zs = o; o = align_up(o + planes);   // per-plane solid flags
     L.partial = o; o = align_up(o + sizeof(double) * 4 * lbmk::RED_BLOCKS);
     L.sums = o; o = align_up(o + sizeof(double) * 4);
     L.status = o; o = align_up(o + sizeof(int) * 4);
@@ -215,7 +217,7 @@ dim3 node_grid(const Geo &g)
 int ensure_memory(lbm_ctx *h)
 {
     if (h->fv[0]) return LBM_OK;
-    Layout L = layout_for(h->D, h->Q, h->geo.N, h->storage);
+    Layout L = layout_for(h->D, h->Q, h->geo.N, h->storage, h->geof.nz);
     if (!h->base) {
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, L.total);
@@ -238,10 +240,19 @@ int ensure_memory(lbm_ctx *h)
     h->u = reinterpret_cast<double *>(b + L.u);
     h->gflux = reinterpret_cast<double *>(b + L.g);
     h->mask = reinterpret_cast<uint8_t *>(b + L.mask);
+    h->geof.zsolid = reinterpret_cast<const uint8_t *>(b + L.zs);
     h->partial = reinterpret_cast<double *>(b + L.partial);
     h->sums = reinterpret_cast<double *>(b + L.sums);
     h->status = reinterpret_cast<int *>(b + L.status);
     CU(h, cudaMemcpyAsync(h->mask, h->mask_host.data(), h->geo.N, cudaMemcpyHostToDevice, h->stream));
+    {   // planes of the fused step's march axis (z; the 2D y axis for D2Q9) that hold a solid
+        const size_t plane = (size_t)h->geof.nx * h->geof.ny;
+        h->zsolid_host.assign(h->geof.nz, 0);
+        for (size_t n = 0; n < h->geo.N; ++n)
+            if (h->mask_host[n]) h->zsolid_host[n / plane] = 1;
+        CU(h, cudaMemcpyAsync(const_cast<uint8_t *>(h->geof.zsolid), h->zsolid_host.data(), h->geof.nz,
+                              cudaMemcpyHostToDevice, h->stream));
+    }
     CU(h, cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
@@ -311,6 +322,17 @@ void launch_fused_tm(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
         h->geof, h->physf, h->mask, src, dst, h->status);
 }
 
+template <bool MASK>
+void launch_fused_wstm(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    using L = lbmf::LatF<1>;
+    const int bytes = (int)sizeof(lbmf::SharedWS<1>);
+    smem_opt_in(lbmf::k_step_f32_wstm<1, MASK>, bytes, done);
+    lbmf::k_step_f32_wstm<1, MASK><<<fused_grid<1>(h->geof), 2 * L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, src, dst, h->status);
+}
+
 template <int LAT, bool MASK>
 void launch_fused_ws(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
@@ -356,6 +378,11 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
         else              launch_fused_tm<LAT, false>(h, s, src, dst);
         return;
     }
+    if (LAT == 1 && h->variant == LBM_FUSED_WS_TMEM) {   // D3Q27, 32 x 8 tiles
+        if (has_solid(h)) launch_fused_wstm<true>(h, s, src, dst);
+        else              launch_fused_wstm<false>(h, s, src, dst);
+        return;
+    }
     static std::atomic<unsigned long long> done_m{0}, done_f{0};   // devices already opted in
     using L = lbmf::LatF<LAT>;
     const int bytes = (int)sizeof(lbmf::SharedF<LAT>);
@@ -384,10 +411,23 @@ void launch_shifted_e(lbm_ctx *h, cudaStream_t s, int k)
 }
 
 template <int LAT, typename ST>
+void launch_shifted_tm(lbm_ctx *h, cudaStream_t s, int k)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
+    smem_opt_in(lbmf::k_step_shifted_tm<LAT, ST>, bytes, done);
+    using L = lbmf::LatF<LAT>;
+    lbmf::k_step_shifted_tm<LAT, ST><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
+        h->rs[k], h->rs[k ^ 1], h->status);
+}
+
+template <int LAT, typename ST>
 void launch_shifted_t(lbm_ctx *h, cudaStream_t s, int k)
 {
     if (h->e64) launch_shifted_e<LAT, ST, true>(h, s, k);
-    else        launch_shifted_e<LAT, ST, false>(h, s, k);
+    else if (h->variant == LBM_FUSED_TMEM) launch_shifted_tm<LAT, ST>(h, s, k);
+    else launch_shifted_e<LAT, ST, false>(h, s, k);
 }
 
 template <int LAT>
@@ -730,7 +770,7 @@ size_t lbm_required_bytes(int lattice, int nx, int ny, int nz, int storage)
 {
     if (!valid_shape(lattice, nx, ny, nz) || storage < LBM_F64 || storage > LBM_BF16S) return 0;
     const int D = lattice == LBM_D2Q9 ? 2 : 3, Q = lattice == LBM_D2Q9 ? 9 : 27;
-    return layout_for(D, Q, (size_t)nx * ny * nz, storage).total;
+    return layout_for(D, Q, (size_t)nx * ny * nz, storage, lattice == LBM_D2Q9 ? ny : nz).total;
 }
 
 int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, double t_over_tc,
@@ -864,7 +904,7 @@ int lbm_bind_device_memory(lbm_handle h, void *dev, size_t bytes)
     if (!h || !dev) return LBM_EINVAL;
     if (h->fv[0]) return fail(h, LBM_ESTATE, "device memory already in use");
     if (reinterpret_cast<uintptr_t>(dev) % kAlign) return fail(h, LBM_EINVAL, "memory not 256-byte aligned");
-    const size_t need = layout_for(h->D, h->Q, h->geo.N, h->storage).total;
+    const size_t need = layout_for(h->D, h->Q, h->geo.N, h->storage, h->geof.nz).total;
     if (bytes < need) return fail(h, LBM_ENOMEM, "bound memory %zu < required %zu", bytes, need);
     h->base = dev;
     h->owns_base = false;
@@ -1461,10 +1501,12 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     const int variant0 = h->variant;
     int best = h->geof.chunk, best_rows = h->tile_rows, best_variant = h->variant;
     double best_ms = 1e30;
-    for (int var = 0; var < (fp32 ? 3 : 1) && rc == LBM_OK; ++var) {
+    for (int var = 0; var <= LBM_FUSED_WS_TMEM && rc == LBM_OK; ++var) {
+        if (var > 0 && (h->e64 || (!fp32 && var != LBM_FUSED_TMEM))) continue;
+        if (var == LBM_FUSED_WS_TMEM && h->lattice != LBM_D3Q27) continue;
         h->variant = var;
         for (int rows : {8, 7}) {
-            if (rows == 7 && !two_heights) continue;
+            if (rows == 7 && (!two_heights || var == LBM_FUSED_WS_TMEM)) continue;
             h->tile_rows = rows;
             for (int c : cands) {
                 if (c > nz && c != cands[0]) continue;
@@ -1521,6 +1563,8 @@ int lbm_set_tile(lbm_handle h, int tile_y)
         return fail(h, LBM_EINVAL, "the tile height is a parameter of the D3Q27 FP32 step only");
     if (tile_y != 7 && tile_y != 8) return fail(h, LBM_EINVAL, "tile height must be 7 or 8");
     if (tile_y == 7 && h->e64) return fail(h, LBM_EINVAL, "the FP64-EOS step runs 8-row tiles");
+    if (tile_y == 7 && h->variant == LBM_FUSED_WS_TMEM)
+        return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory form runs 8-row tiles");
     if (h->tile_rows != tile_y && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -1532,11 +1576,16 @@ int lbm_set_tile(lbm_handle h, int tile_y)
 int lbm_set_fused_variant(lbm_handle h, int variant)
 {
     if (!h) return LBM_EINVAL;
-    if (variant < LBM_FUSED_PLAIN || variant > LBM_FUSED_TMEM)
+    if (variant < LBM_FUSED_PLAIN || variant > LBM_FUSED_WS_TMEM)
         return fail(h, LBM_EINVAL, "unknown fused-step variant %d", variant);
-    if ((h->storage != LBM_F32 || h->e64) && variant != LBM_FUSED_PLAIN)
-        return fail(h, LBM_EINVAL, "the fused-step variants are forms of the FP32 step only "
-                                   "(without LBM_FLAG_EOS_F64)");
+    if (variant == LBM_FUSED_WS_TMEM && (h->lattice != LBM_D3Q27 || h->tile_rows != 8))
+        return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory form runs D3Q27 32 x 8 tiles");
+    if (h->storage == LBM_F64 && variant != LBM_FUSED_PLAIN)
+        return fail(h, LBM_EINVAL, "the FP64 step has one form");
+    if (h->e64 && variant != LBM_FUSED_PLAIN)
+        return fail(h, LBM_EINVAL, "the FP64-EOS step has one form");
+    if (shifted(h->storage) && (variant == LBM_FUSED_WARP_SPECIALISED || variant == LBM_FUSED_WS_TMEM))
+        return fail(h, LBM_EINVAL, "the warp-specialised forms are forms of the FP32 step only");
     if (h->variant != variant && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;

@@ -50,7 +50,20 @@ struct GeoF {
     int nx, ny, nz;   // as stored; D2Q9: ny = 1 and nz = the 2D y extent
     unsigned N;
     int chunk;        // planes per CTA along z
+    const uint8_t *zsolid;   // per plane along z: 1 if it holds a solid node (masked lattices)
 };
+
+// Masked lattices: whether plane z (wrapped) holds a solid node, and
+// whether any of the planes z-1, z, z+1 do (the planes a collision at z
+// pushes into). Planes without solids run the unmasked code.
+__device__ __forceinline__ bool plane_solid(const GeoF &g, int z)
+{
+    return g.zsolid[z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z)] != 0;
+}
+__device__ __forceinline__ bool planes_solid3(const GeoF &g, int z)
+{
+    return plane_solid(g, z - 1) || plane_solid(g, z) || plane_solid(g, z + 1);
+}
 
 struct PhysF {
     int eos;
@@ -165,6 +178,18 @@ __device__ __forceinline__ double excess_pressure_d(const PhysF &p, double rho)
     }
 }
 
+// Sum of v[0..n-1] as a balanced tree of additions.
+template <int N>
+__device__ __forceinline__ float pairwise_sum(const float *v)
+{
+    if constexpr (N == 1) {
+        return v[0];
+    } else {
+        constexpr int H = N / 2;
+        return pairwise_sum<H>(v) + pairwise_sum<N - H>(v + H);
+    }
+}
+
 __device__ __forceinline__ int wrapf(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -234,14 +259,14 @@ __device__ __forceinline__ unsigned smem_u32(const void *ptr)
 // node) and phase B, two planes later, needs them again. Instead of a
 // second read through L2, the thread keeps them in its own lane of the
 // SM's Tensor Memory (tcgen05.st / tcgen05.ld, 32 x 32-bit per lane and
-// column), three plane slots deep. Warp w reaches lanes 32 (w % 4) ..
+// column), four plane slots deep. Warp w reaches lanes 32 (w % 4) ..
 // 32 (w % 4) + 31, so warps w and w + 4 share lanes and take separate
 // column ranges. The block allocates TmemF::COLS columns (256 for D3Q27
 // tiles, two blocks per SM fill the 512) and frees them before it exits.
 template <int LAT> struct TmemF {
     static constexpr int Q = LatF<LAT>::Q;
     static constexpr int CPS = Q <= 16 ? 16 : 32;          // columns per plane slot
-    static constexpr int SLOTS = 3;
+    static constexpr int SLOTS = 4;   // planes pl - 2 .. pl + 1 (the warp-specialised form needs 4)
     static constexpr int WARPS = LatF<LAT>::TX * LatF<LAT>::TY / 32;
     static constexpr int NEED = (WARPS + 3) / 4 * SLOTS * CPS;
     static constexpr int COLS = NEED <= 32 ? 32 : NEED <= 64 ? 64 : NEED <= 128 ? 128 : NEED <= 256 ? 256 : 512;
@@ -252,8 +277,9 @@ template <int LAT>
 __device__ __forceinline__ unsigned tmem_slot(unsigned base, int slot)
 {
     using T = TmemF<LAT>;
-    const int w = threadIdx.x >> 5;
-    return base + ((unsigned)(32 * (w & 3)) << 16) + (unsigned)((w >> 2) * T::SLOTS * T::CPS + slot * T::CPS);
+    const int w = threadIdx.x >> 5;   // warps w and w + 8 (a producer and its consumer) share a lane range
+    return base + ((unsigned)(32 * (w & 3)) << 16) +
+           (unsigned)(((w & 7) >> 2) * T::SLOTS * T::CPS + slot * T::CPS);
 }
 
 __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -402,6 +428,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
     constexpr int KA = (AX * AY + NT - 1) / NT;
     const int zl = wrapf(z0 - 2 + pl, g.nz);
     const int rs = pl % RS, gs = pl % GS;
+    const bool msk = MASK && g.zsolid[zl];   // the plane holds a solid node
     float fi[KA][Q];
     unsigned nk[KA];
     bool live[KA], solid[KA];
@@ -413,7 +440,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
         int r, c;
         halo_rc<LAT>(live[u] ? k : 0, r, c);
         nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
-        solid[u] = MASK && live[u] && mask[nk[u]];
+        solid[u] = MASK && live[u] && msk && mask[nk[u]];
         if (live[u] && !solid[u]) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
@@ -431,27 +458,22 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
             rho = p.rho_w;
             d = p.spsi_w;
         } else {
-            // x-row sums for each (cy, cz), then the moments from them
+            // x-row sums for each (cy, cz), then the moments from them, each
+            // summed pairwise (short dependency chains)
             constexpr int R = Q / 3;
-            float row[R], jx = 0.0f;
+            float row[R], dx[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                row[q] = fi[u][3 * q] + fi[u][3 * q + 1] + fi[u][3 * q + 2];
-                jx += fi[u][3 * q + 2] - fi[u][3 * q];
+                row[q] = (fi[u][3 * q] + fi[u][3 * q + 1]) + fi[u][3 * q + 2];
+                dx[q] = fi[u][3 * q + 2] - fi[u][3 * q];
             }
-            rho = 0.0f;
-#pragma unroll
-            for (int q = 0; q < R; ++q) rho += row[q];
+            rho = pairwise_sum<R>(row);
+            const float jx = pairwise_sum<R>(dx);
             if (ring1) {
-                float jy = 0.0f, jz = 0.0f;
-#pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const int cy = THREE ? q % 3 - 1 : 0, cz = THREE ? q / 3 - 1 : q - 1;
-                    if (cy > 0) jy += row[q];
-                    if (cy < 0) jy -= row[q];
-                    if (cz > 0) jz += row[q];
-                    if (cz < 0) jz -= row[q];
-                }
+                // D3Q27 rows q = (cy + 1) + 3 (cz + 1); D2Q9 rows q = cz + 1
+                const float jy = THREE ? ((row[2] + row[5]) + row[8]) - ((row[0] + row[3]) + row[6]) : 0.0f;
+                const float jz = THREE ? ((row[6] + row[7]) + row[8]) - ((row[0] + row[1]) + row[2])
+                                       : row[R - 1] - row[0];
                 const float inv = __frcp_rn(rho);
                 const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
                 gx = rho * ux * ux * ux;
@@ -483,7 +505,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
     // the thread's interior node (its halo node tid), for phase B two planes on
     if constexpr (TM) {
         __syncwarp();   // tcgen05.st is warp-collective: reconverge after the loops
-        tmem_store_pop<Q>(tmem_slot<LAT>(tbase, pl % 3), fi[0]);
+        tmem_store_pop<Q>(tmem_slot<LAT>(tbase, pl & 3), fi[0]);
     }
 }
 
@@ -521,10 +543,10 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
     float fi[Q];
     if constexpr (TM) {
         __syncwarp();   // tcgen05.ld is warp-collective
-        tmem_load_pop<Q>(tmem_slot<LAT>(tbase, pc % 3), fi);
+        tmem_load_pop<Q>(tmem_slot<LAT>(tbase, pc & 3), fi);
         if (!inside) return;
     }
-    if (!(MASK && mask[n])) {
+    if (!(MASK && g.zsolid[zc] && mask[n])) {
         if constexpr (!TM) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
@@ -673,16 +695,31 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
         const int X[3] = {wrapf(xi - 1, g.nx), xi, wrapf(xi + 1, g.nx)};
         const int Y[3] = {THREE ? wrapf(yi - 1, g.ny) : 0, yi, THREE ? wrapf(yi + 1, g.ny) : 0};
         const int Z[3] = {wrapf(zc - 1, g.nz), zc, wrapf(zc + 1, g.nz)};
+        // Solids among the destinations are looked up only where one of the
+        // planes zc - 1 .. zc + 1 holds a solid node.
+        if (MASK && planes_solid3(g, zc)) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-            const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
-            const float post = SHIFT ? fmaf(fmaf(omw, fi[i] - es.x, es.y), inv, -weight_f<LAT>(i))
-                                     : fmaf(omw, fi[i] - es.x, es.y);
-            const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
-                                 plane * (unsigned)Z[cz + 1];
-            if (MASK && mask[dst]) fout[(Q - 1 - i) * N + n] = from_f<ST>(post);
-            else                   fout[i * N + dst] = from_f<ST>(post);
+            for (int i = 0; i < Q; ++i) {
+                const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+                const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
+                const float post = SHIFT ? fmaf(fmaf(omw, fi[i] - es.x, es.y), inv, -weight_f<LAT>(i))
+                                         : fmaf(omw, fi[i] - es.x, es.y);
+                const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
+                                     plane * (unsigned)Z[cz + 1];
+                if (mask[dst]) fout[(Q - 1 - i) * N + n] = from_f<ST>(post);
+                else           fout[i * N + dst] = from_f<ST>(post);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+                const float2 es = __fmul2_rn(A[cx + 1][cy + 1], ES[2][cz + 1]);   // (feq, f*)
+                const float post = SHIFT ? fmaf(fmaf(omw, fi[i] - es.x, es.y), inv, -weight_f<LAT>(i))
+                                         : fmaf(omw, fi[i] - es.x, es.y);
+                const unsigned dst = (unsigned)X[cx + 1] + (unsigned)g.nx * (unsigned)Y[cy + 1] +
+                                     plane * (unsigned)Z[cz + 1];
+                fout[i * N + dst] = from_f<ST>(post);
+            }
         }
     }
 }
@@ -768,14 +805,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     }
 }
 
-template <int LAT, bool MASK>
+template <int LAT, bool MASK, bool TM = false>
 __device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
                                               const uint8_t *__restrict__ mask,
                                               const float *__restrict__ f, float *__restrict__ fout,
                                               int *__restrict__ status, int bx, int by, int bz,
-                                              SharedWS<LAT> &sm)
+                                              SharedWS<LAT> &sm, unsigned tbase = 0)
 {
-    constexpr int NT = LatF<LAT>::TX * LatF<LAT>::TY;
+    constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
+    static_assert(!TM || NT % 256 == 0, "a consumer warp shares its producer's Tensor Memory lanes");
     const int tid = threadIdx.x;
     const TileF T = tile_setup<LAT, float>(g, bx, by, bz, sm, tid, 2 * NT, nullptr);
     if (tid == 0)
@@ -784,26 +822,37 @@ __device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
             mbar_init(&sm.empty[k], NT);
         }
     __syncthreads();
+    // A wait that runs out sets bit 2 of the status and ends this group's
+    // loop; the other group's next wait then runs out too, so every thread
+    // reaches the end of the tile (where the caller may free Tensor Memory).
     if (tid < NT) {
         for (int pl = 0; pl < T.np; ++pl) {
             if (pl >= 6 && !mbar_wait(&sm.empty[(pl - 2) % 6], ((pl - 6) / 6) & 1)) {
                 atomicOr(status, 2);
-                return;
+                break;
             }
-            phase_a<LAT, MASK>(g, p, mask, f, sm, T, pl, tid, nullptr);
+            if constexpr (TM) tmem_fence_after();
+            phase_a<LAT, MASK, TM>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase);
+            if constexpr (TM) tmem_fence_before();
             mbar_arrive(&sm.full[pl % 6]);
         }
     } else {
         const int t = tid - NT;
-        constexpr int TX = LatF<LAT>::TX;
         const bool inside = T.x0 + t % TX < g.nx && T.y0 + t / TX < g.ny;
         for (int pl = 0; pl < T.np; ++pl) {
             if (!mbar_wait(&sm.full[pl % 6], (pl / 6) & 1)) {
                 atomicOr(status, 2);
-                return;
+                break;
             }
             if (pl >= 4) {
-                if (inside) phase_b<LAT, MASK>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr);
+                if constexpr (TM) {
+                    tmem_fence_after();
+                    phase_b<LAT, MASK, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr, tbase,
+                                             inside);
+                    tmem_fence_before();
+                } else if (inside) {
+                    phase_b<LAT, MASK>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr);
+                }
                 mbar_arrive(&sm.empty[pl % 6]);
             }
         }
@@ -820,6 +869,31 @@ k_step_f32_ws(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SharedWS<LAT> &sm = *reinterpret_cast<SharedWS<LAT> *>(smem_raw);
     fused_tile_ws<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+}
+
+// Warp-specialised with Tensor Memory staging: the producer that loads an
+// interior node leaves its populations in the Tensor Memory lane of the
+// consumer that collides it (warps w and w + 8 share lanes; 32 x 8 tiles
+// only); the full/empty barriers also order the Tensor Memory accesses.
+template <int LAT, bool MASK>
+__global__ void __launch_bounds__(2 * LatF<LAT>::TX * LatF<LAT>::TY, 1)
+k_step_f32_wstm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__restrict__ f,
+                float *__restrict__ fout, int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedWS<LAT> &sm = *reinterpret_cast<SharedWS<LAT> *>(smem_raw);
+    constexpr unsigned COLS = TmemF<LAT>::COLS;
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned tbase = sm.tmem;
+    fused_tile_ws<LAT, MASK, true>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm,
+                                   tbase);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, COLS);
 }
 
 // FP32 populations; dynamic shared memory of sizeof(SharedF<LAT>).
@@ -873,6 +947,30 @@ k_step_shifted(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
     SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
     fused_tile<LAT, false, ST, SharedS<LAT>, false, E64>(g, p, nullptr, f, fout, status, blockIdx.x,
                                                          blockIdx.y, blockIdx.z, sm, rho_src, rho_dst);
+}
+
+// Shifted 16-bit storage with the interior nodes' decoded populations kept in
+// Tensor Memory between the phases (as k_step_f32_tm).
+template <int LAT, typename ST>
+__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
+k_step_shifted_tm(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
+                  const float *__restrict__ rho_src, float *__restrict__ rho_dst,
+                  int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
+    constexpr unsigned COLS = TmemF<LAT>::COLS;
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned tbase = sm.tmem;
+    fused_tile<LAT, false, ST, SharedS<LAT>, true>(g, p, nullptr, f, fout, status, blockIdx.x,
+                                                   blockIdx.y, blockIdx.z, sm, rho_src, rho_dst, tbase);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, COLS);
 }
 
 // Many lattices of one type and one storage in one launch: descriptor of one

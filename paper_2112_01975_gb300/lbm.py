@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 D2Q9, D3Q27 = 0, 1
 EOS_VDW, EOS_PR, EOS_RKS, EOS_CS, EOS_SC1, EOS_SC2 = 0, 1, 2, 3, 4, 5
 F64, F32, F16S, BF16S = 0, 1, 2, 3
-FUSED_PLAIN, FUSED_WARP_SPECIALISED, FUSED_TMEM = 0, 1, 2
-FUSED_NAMES = {0: "plain", 1: "warp-specialised", 2: "tensor-memory"}
+FUSED_PLAIN, FUSED_WARP_SPECIALISED, FUSED_TMEM, FUSED_WS_TMEM = 0, 1, 2, 3
+FUSED_NAMES = {0: "plain", 1: "warp-specialised", 2: "tensor-memory",
+               3: "warp-specialised, tensor-memory"}
 FLAG_PHI_OFF = 1
 FLAG_EOS_F64 = 2
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",

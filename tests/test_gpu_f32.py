@@ -276,12 +276,12 @@ def pillar_oracle():
     return w, n, mask, rho, o
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_f32_pr_pillars_32cubed_1000_steps(lbm, pillar_oracle, variant):
     """The 32^3 pillar case of the FP64 parity tests (a wall with 4x4x6
     pillars, a Peng-Robinson drop above them) in FP32 storage, with each form
-    of the fused step (plain, warp-specialised, Tensor Memory), against the
-    FP64 oracle after 1000 steps at the FP32 tolerances; the three forms
+    of the fused step (plain, warp-specialised, Tensor Memory, both), against the
+    FP64 oracle after 1000 steps at the FP32 tolerances; the four forms
     agree bitwise."""
     w, n, mask, rho, o = pillar_oracle
 
