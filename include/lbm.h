@@ -75,9 +75,10 @@ enum lbm_eos {
  * (FP16 / BF16) relative deviation h_i = f_i / rho(src) - w_i from the
  * weight, rho(src) the FP32 density of the node that pushed it (the node
  * itself after a bounce-back), with an FP32 density field beside each
- * buffer; the fused
- * step computes in FP32; lattices with solid nodes are refused. Moments,
- * reductions and population I/O are FP64 at the ABI for every storage. */
+ * buffer (-1 at solid nodes, whose fluid neighbours' bounced populations
+ * are stored relative to those neighbours' own densities); the fused step
+ * computes in FP32. Moments, reductions and population I/O are FP64 at the
+ * ABI for every storage. */
 enum lbm_storage { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 };
 
 enum lbm_status {

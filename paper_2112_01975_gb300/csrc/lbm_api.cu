@@ -398,36 +398,43 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
     }
 }
 
-template <int LAT, typename ST, bool E64>
+template <int LAT, typename ST, bool E64, bool MASK>
 void launch_shifted_e(lbm_ctx *h, cudaStream_t s, int k)
 {
     static std::atomic<unsigned long long> done{0};   // devices already opted in
     const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
-    smem_opt_in(lbmf::k_step_shifted<LAT, ST, E64>, bytes, done);
+    smem_opt_in(lbmf::k_step_shifted<LAT, ST, E64, MASK>, bytes, done);
     using L = lbmf::LatF<LAT>;
-    lbmf::k_step_shifted<LAT, ST, E64><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
-        h->geof, h->physf, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
+    lbmf::k_step_shifted<LAT, ST, E64, MASK><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
         h->rs[k], h->rs[k ^ 1], h->status);
 }
 
-template <int LAT, typename ST>
+template <int LAT, typename ST, bool MASK>
 void launch_shifted_tm(lbm_ctx *h, cudaStream_t s, int k)
 {
     static std::atomic<unsigned long long> done{0};   // devices already opted in
     const int bytes = (int)sizeof(lbmf::SharedS<LAT>);
-    smem_opt_in(lbmf::k_step_shifted_tm<LAT, ST>, bytes, done);
+    smem_opt_in(lbmf::k_step_shifted_tm<LAT, ST, MASK>, bytes, done);
     using L = lbmf::LatF<LAT>;
-    lbmf::k_step_shifted_tm<LAT, ST><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
-        h->geof, h->physf, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
+    lbmf::k_step_shifted_tm<LAT, ST, MASK><<<fused_grid<LAT>(h->geof), L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
         h->rs[k], h->rs[k ^ 1], h->status);
+}
+
+template <int LAT, typename ST, bool MASK>
+void launch_shifted_m(lbm_ctx *h, cudaStream_t s, int k)
+{
+    if (h->e64) launch_shifted_e<LAT, ST, true, MASK>(h, s, k);
+    else if (h->variant == LBM_FUSED_TMEM) launch_shifted_tm<LAT, ST, MASK>(h, s, k);
+    else launch_shifted_e<LAT, ST, false, MASK>(h, s, k);
 }
 
 template <int LAT, typename ST>
 void launch_shifted_t(lbm_ctx *h, cudaStream_t s, int k)
 {
-    if (h->e64) launch_shifted_e<LAT, ST, true>(h, s, k);
-    else if (h->variant == LBM_FUSED_TMEM) launch_shifted_tm<LAT, ST>(h, s, k);
-    else launch_shifted_e<LAT, ST, false>(h, s, k);
+    if (has_solid(h)) launch_shifted_m<LAT, ST, true>(h, s, k);
+    else              launch_shifted_m<LAT, ST, false>(h, s, k);
 }
 
 template <int LAT>
@@ -508,7 +515,9 @@ template <int LAT>
 int encode_from(lbm_ctx *h, const double *f)
 {
     const dim3 gr = node_grid(h->geo), bl = node_block(h->geo);
-    lbmk::k_density<LAT><<<gr, bl, 0, h->stream>>>(h->geo, f, h->rs[0]);
+    // both buffers' source densities: -1 at solid nodes stays for good
+    lbmk::k_density<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->mask, f, h->rs[0]);
+    lbmk::k_density<LAT><<<gr, bl, 0, h->stream>>>(h->geo, h->mask, f, h->rs[1]);
     if (h->storage == LBM_F16S)
         lbmk::k_encode_shifted<LAT, __half><<<gr, bl, 0, h->stream>>>(
             h->geo, f, h->rs[0], static_cast<__half *>(h->fv[0]));
@@ -516,7 +525,7 @@ int encode_from(lbm_ctx *h, const double *f)
         lbmk::k_encode_shifted<LAT, __nv_bfloat16><<<gr, bl, 0, h->stream>>>(
             h->geo, f, h->rs[0], static_cast<__nv_bfloat16 *>(h->fv[0]));
     CU(h, cudaGetLastError());
-    h->launches += 2;
+    h->launches += 3;
     h->cur = 0;
     return LBM_OK;
 }
@@ -785,9 +794,6 @@ int lbm_create(lbm_handle *out, int lattice, int nx, int ny, int nz, int eos, do
     if (p) prm = *p;
     else lbm_default_params(eos, &prm);
     if (prm.storage < LBM_F64 || prm.storage > LBM_BF16S) return LBM_EINVAL;
-    if (shifted(prm.storage) && solid_mask)
-        for (size_t n = 0; n < (size_t)nx * ny * nz; ++n)
-            if (solid_mask[n]) return LBM_EINVAL;   // shifted storage: lattices without solids
     if (!(prm.a > 0.0) || !(prm.b > 0.0) || !(prm.rho_w > 0.0)) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(prm.g[a])) return LBM_EINVAL;

@@ -220,14 +220,19 @@ template <int LAT> struct SharedS : SharedF<LAT> {
 };
 
 // Population i of the node at halo coordinates (r, c) of ring plane q:
-// stored value plus w_i times the density of its source node.
-template <int LAT, typename ST, typename SM>
+// stored value plus w_i times the density of its source node. With solid
+// nodes (MASK), a population whose source r - c_i is solid was bounced back
+// by the node itself and stored relative to the node's own density: solid
+// nodes hold -1 in the source-density field, which selects the node's own.
+template <int LAT, bool MASK = false, typename ST, typename SM>
 __device__ __forceinline__ float decode_pop(ST hv, int i, int r, int c, int q, const SM &sm)
 {
     if constexpr (IsShifted<ST>::value) {
         using L = LatF<LAT>;
         const int rr = r + (LAT == 1 ? 1 : 0) - L::cy(i), cc = c + 1 - L::cx(i);
-        return (weight_f<LAT>(i) + to_f(hv)) * sm.rs[(q - L::cz(i) + SM::QS) & (SM::QS - 1)][rr][cc];
+        float src = sm.rs[(q - L::cz(i) + SM::QS) & (SM::QS - 1)][rr][cc];
+        if (MASK && src < 0.0f) src = sm.rs[(q + SM::QS) & (SM::QS - 1)][r + (LAT == 1 ? 1 : 0)][c + 1];
+        return (weight_f<LAT>(i) + to_f(hv)) * src;
     } else {
         return to_f(hv);
     }
@@ -443,7 +448,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
         solid[u] = MASK && live[u] && msk && mask[nk[u]];
         if (live[u] && !solid[u]) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
+            for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT, MASK>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
         }
     }
 #pragma unroll
@@ -549,7 +554,7 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
     if (!(MASK && g.zsolid[zc] && mask[n])) {
         if constexpr (!TM) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
+            for (int i = 0; i < Q; ++i) fi[i] = decode_pop<LAT, MASK>(__ldg(f + (i * N + n)), i, ty + HY, tx + 2, pc, sm);
         }
         const int cr = ty + HY, cc = tx + 2;
         const float2 c0 = s_rp[pc % RS][cr][cc];
@@ -737,7 +742,6 @@ __device__ __forceinline__ void fused_tile(const GeoF &g, const PhysF &p,
                                            float *__restrict__ rho_dst = nullptr,
                                            unsigned tbase = 0)
 {
-    static_assert(!(IsShifted<ST>::value && MASK), "shifted storage runs lattices without solid nodes");
     constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
     const int tid = threadIdx.x;
     const TileF T = tile_setup<LAT, ST>(g, bx, by, bz, sm, tid, NT, rho_src);
@@ -937,24 +941,24 @@ k_step_f32_tm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *__
 // Shifted 16-bit storage (ST = __half or __nv_bfloat16): populations h_i
 // with the source densities rho_src read and rho_dst written; dynamic shared
 // memory of sizeof(SharedS<LAT>).
-template <int LAT, typename ST, bool E64 = false>
+template <int LAT, typename ST, bool E64 = false, bool MASK = false>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
-k_step_shifted(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
-               const float *__restrict__ rho_src, float *__restrict__ rho_dst,
+k_step_shifted(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const ST *__restrict__ f,
+               ST *__restrict__ fout, const float *__restrict__ rho_src, float *__restrict__ rho_dst,
                int *__restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SharedS<LAT> &sm = *reinterpret_cast<SharedS<LAT> *>(smem_raw);
-    fused_tile<LAT, false, ST, SharedS<LAT>, false, E64>(g, p, nullptr, f, fout, status, blockIdx.x,
-                                                         blockIdx.y, blockIdx.z, sm, rho_src, rho_dst);
+    fused_tile<LAT, MASK, ST, SharedS<LAT>, false, E64>(g, p, mask, f, fout, status, blockIdx.x,
+                                                        blockIdx.y, blockIdx.z, sm, rho_src, rho_dst);
 }
 
 // Shifted 16-bit storage with the interior nodes' decoded populations kept in
 // Tensor Memory between the phases (as k_step_f32_tm).
-template <int LAT, typename ST>
+template <int LAT, typename ST, bool MASK = false>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
-k_step_shifted_tm(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fout,
-                  const float *__restrict__ rho_src, float *__restrict__ rho_dst,
+k_step_shifted_tm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const ST *__restrict__ f,
+                  ST *__restrict__ fout, const float *__restrict__ rho_src, float *__restrict__ rho_dst,
                   int *__restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -965,8 +969,8 @@ k_step_shifted_tm(GeoF g, PhysF p, const ST *__restrict__ f, ST *__restrict__ fo
     __syncthreads();
     tmem_fence_after();
     const unsigned tbase = sm.tmem;
-    fused_tile<LAT, false, ST, SharedS<LAT>, true>(g, p, nullptr, f, fout, status, blockIdx.x,
-                                                   blockIdx.y, blockIdx.z, sm, rho_src, rho_dst, tbase);
+    fused_tile<LAT, MASK, ST, SharedS<LAT>, true>(g, p, mask, f, fout, status, blockIdx.x,
+                                                  blockIdx.y, blockIdx.z, sm, rho_src, rho_dst, tbase);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
@@ -1014,7 +1018,7 @@ k_step_f32_batch(const MemberF *__restrict__ members, const WorkItem *__restrict
     }
 }
 
-// The same over members with 16-bit shifted storage (no solid nodes);
+// The same over members with 16-bit shifted storage;
 // dynamic shared memory of sizeof(SharedS<LAT>).
 template <int LAT, typename ST>
 __global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
@@ -1026,9 +1030,14 @@ k_step_shifted_batch(const MemberF *__restrict__ members, const WorkItem *__rest
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         const MemberF &m = members[w.member];
-        fused_tile<LAT, false, ST, SharedS<LAT>>(m.g, m.p, nullptr, static_cast<const ST *>(m.src),
-                                                static_cast<ST *>(m.dst), m.status, w.bx, w.by,
-                                                w.bz, sm, m.rho_src, m.rho_dst);
+        if (m.mask)
+            fused_tile<LAT, true, ST, SharedS<LAT>>(m.g, m.p, m.mask, static_cast<const ST *>(m.src),
+                                                   static_cast<ST *>(m.dst), m.status, w.bx, w.by,
+                                                   w.bz, sm, m.rho_src, m.rho_dst);
+        else
+            fused_tile<LAT, false, ST, SharedS<LAT>>(m.g, m.p, nullptr, static_cast<const ST *>(m.src),
+                                                    static_cast<ST *>(m.dst), m.status, w.bx, w.by,
+                                                    w.bz, sm, m.rho_src, m.rho_dst);
         __syncthreads();
     }
 }

@@ -580,18 +580,29 @@ __global__ void k_decode_shifted(Geo g, const ST *__restrict__ h, const float *_
     const int y = blockIdx.y, z = blockIdx.z;
     const unsigned n = x + g.nx * (y + g.ny * z);
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        f[(size_t)i * g.N + n] = (weight_d(i, D) + (double)lbmf::to_f(h[(size_t)i * g.N + n])) *
-                                 (double)rho_src[source_node(g, D, i, x, y, z)];
+    for (int i = 0; i < Q; ++i) {
+        // a solid source (density -1) means a population bounced by n itself
+        float src = rho_src[source_node(g, D, i, x, y, z)];
+        if (src < 0.0f) src = rho_src[n];
+        f[(size_t)i * g.N + n] = (weight_d(i, D) + (double)lbmf::to_f(h[(size_t)i * g.N + n])) * (double)src;
+    }
 }
 
+// The source-density field of shifted storage: each fluid node's density,
+// -1 at solid nodes (their populations' sources are the fluid nodes that
+// bounced them; see the decoders).
 template <int LAT>
-__global__ void k_density(Geo g, const double *__restrict__ f, float *__restrict__ rho)
+__global__ void k_density(Geo g, const uint8_t *__restrict__ mask, const double *__restrict__ f,
+                          float *__restrict__ rho)
 {
     constexpr int Q = Lattice<LAT>::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= g.nx) return;
     const unsigned n = x + g.nx * (blockIdx.y + g.ny * blockIdx.z);
+    if (mask[n]) {
+        rho[n] = -1.0f;
+        return;
+    }
     double s = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) s += f[(size_t)i * g.N + n];
@@ -607,10 +618,18 @@ __global__ void k_encode_shifted(Geo g, const double *__restrict__ f, const floa
     if (x >= g.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const unsigned n = x + g.nx * (y + g.ny * z);
+    if (rho[n] < 0.0f) {   // solid: no populations
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        h[(size_t)i * g.N + n] = lbmf::from_f<ST>(
-            (float)(f[(size_t)i * g.N + n] / (double)rho[source_node(g, D, i, x, y, z)] - weight_d(i, D)));
+        for (int i = 0; i < Q; ++i) h[(size_t)i * g.N + n] = lbmf::from_f<ST>(0.0f);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float src = rho[source_node(g, D, i, x, y, z)];
+        if (src < 0.0f) src = rho[n];   // bounced by n itself
+        h[(size_t)i * g.N + n] =
+            lbmf::from_f<ST>((float)(f[(size_t)i * g.N + n] / (double)src - weight_d(i, D)));
+    }
 }
 
 // Element-wise type conversion (population I/O of FP32 storage).
