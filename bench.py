@@ -96,10 +96,10 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 7, 8],
                     help="D3Q27 FP32 tile height (0: picked by the autotuner, or 8 with --chunk)")
-    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="fused-step form: 0 plain, 1 warp-specialised, 2 Tensor Memory, 3 "
-                         "warp-specialised with Tensor Memory (-1: picked by the autotuner, "
-                         "or plain with --chunk)")
+                         "warp-specialised with Tensor Memory, 4 the same with TMA-staged planes "
+                         "(-1: picked by the autotuner, or plain with --chunk)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--eos64", action="store_true",
@@ -590,7 +590,9 @@ def main():
                                1: "k_step_f32_ws (fused step, warp-specialised)",
                                2: "k_step_f32_tm (fused step, Tensor Memory staging)",
                                3: "k_step_f32_wstm (fused step, warp-specialised, Tensor Memory "
-                                  "staging)"}[variant]
+                                  "staging)",
+                               4: "k_step_f32_wstma (fused step, warp-specialised, Tensor Memory "
+                                  "staging, TMA-staged planes)"}[variant]
                     if storage == F32 else
                     ("k_step_shifted_tm" if variant == 2 else "k_step_shifted"),
                     "peak_source": peak_kind + " hbm_gbs (burst copy)",

@@ -295,16 +295,31 @@ int lbm_set_tile(lbm_handle h, int tile_y);
  *     SM's Tensor Memory from the plane's entry to its collision instead of
  *     being read twice; each block holds 256 columns (D3Q27; 64 for D2Q9) of
  *     Tensor Memory while it runs. */
-enum { LBM_FUSED_PLAIN = 0, LBM_FUSED_WARP_SPECIALISED = 1, LBM_FUSED_TMEM = 2, LBM_FUSED_WS_TMEM = 3 };
+enum {
+    LBM_FUSED_PLAIN = 0,
+    LBM_FUSED_WARP_SPECIALISED = 1,
+    LBM_FUSED_TMEM = 2,
+    LBM_FUSED_WS_TMEM = 3,
+    LBM_FUSED_WS_TMA = 4
+};
 
 /*   LBM_FUSED_WS_TMEM (D3Q27 FP32, 32 x 8 tiles): the warp-specialised form
  *     with the Tensor Memory staging, the producer that loads a node leaving
  *     its populations in the lane of the consumer that collides it.
+ *   LBM_FUSED_WS_TMA (D3Q27 FP32, 32 x 8 tiles, nx a multiple of 4): the
+ *     LBM_FUSED_WS_TMEM form with each entering plane's populations on the
+ *     tile's halo copied into shared memory by the tensor-memory-access unit
+ *     (one bulk tensor copy per plane, requested two planes ahead) instead
+ *     of loaded by the producers; 215 KB of shared memory per block. The
+ *     tensor maps are made when the handle's device memory is laid out; if
+ *     the driver offers no tensor-map encoder there, a handle set to this
+ *     form runs LBM_FUSED_WS_TMEM (lbm_get_fused_variant says which).
  * Select a form of the fused step (lbm_autotune times the forms the
  * storage has). LBM_EINVAL for an unknown form, a form other than
  * LBM_FUSED_PLAIN with LBM_F64 storage or LBM_FLAG_EOS_F64, or the
- * warp-specialised forms with shifted storage, or LBM_FUSED_WS_TMEM with D2Q9
- * or 7-row tiles. */
+ * warp-specialised forms with shifted storage, or LBM_FUSED_WS_TMEM or
+ * LBM_FUSED_WS_TMA with D2Q9 or 7-row tiles, or LBM_FUSED_WS_TMA with nx not a
+ * multiple of 4 or, after the memory is laid out, without tensor maps. */
 int lbm_set_fused_variant(lbm_handle h, int variant);
 
 /* *variant = the form of the fused step in use. */

@@ -1,4 +1,5 @@
 // C ABI of the two-phase lattice Boltzmann library (declared in include/lbm.h).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +57,10 @@ struct lbm_ctx {
     int *poll_host = nullptr;
     cudaEvent_t poll_ev = nullptr;
     bool poll_pending = false;
+    // D3Q27 FP32 with nx % 4 == 0: the two population buffers as 4D tensors
+    // (x, y, z, i) for the TMA-staged form (LBM_FUSED_WS_TMA)
+    lbmf::BoxMaps tmaps[2];
+    bool tmap_ready = false;
     // interpolated bounce-back: boundary nodes, their active links, wall distances
     int nb = 0;
     unsigned *bn = nullptr, *bmask = nullptr;
@@ -214,6 +219,8 @@ dim3 node_grid(const Geo &g)
     return dim3((g.nx + b.x - 1) / b.x, g.ny, g.nz);
 }
 
+void make_tensor_maps(lbm_ctx *h);
+
 int ensure_memory(lbm_ctx *h)
 {
     if (h->fv[0]) return LBM_OK;
@@ -255,10 +262,53 @@ int ensure_memory(lbm_ctx *h)
     }
     CU(h, cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
+    make_tensor_maps(h);
+    if (h->variant == LBM_FUSED_WS_TMA && !h->tmap_ready) h->variant = LBM_FUSED_WS_TMEM;
     return LBM_OK;
 }
 
 bool has_solid(const lbm_ctx *h) { return h->any_solid; }
+
+// The two population buffers of a D3Q27 FP32 handle as 4D tensors (x, y, z,
+// i) of FP32, each with the four box shapes of the TMA-staged form (32 x 8,
+// 32 x 2, 4 x 8 and 4 x 2 nodes of one plane, all 27 populations). Needs
+// nx % 4 == 0 (16-byte row strides) and the driver's tensor-map encoder,
+// found through the runtime's entry-point query; leaves tmap_ready false
+// when either is missing.
+void make_tensor_maps(lbm_ctx *h)
+{
+    h->tmap_ready = false;
+    if (h->lattice != LBM_D3Q27 || h->storage != LBM_F32 || h->geo.nx % 4 || !h->fv[0]) return;
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return;
+    }
+    const Geo &g = h->geo;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 27};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)g.N * 4};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int k = 0; k < 2; ++k) {
+        CUtensorMap *m[4] = {&h->tmaps[k].mc, &h->tmaps[k].tc, &h->tmaps[k].ml, &h->tmaps[k].tl};
+        const cuuint32_t wx[4] = {32, 32, 4, 4}, wy[4] = {8, 2, 8, 2};
+        for (int j = 0; j < 4; ++j) {
+            const cuuint32_t box[4] = {wx[j], wy[j], 1, 27};
+            if (reinterpret_cast<Encode>(fn)(m[j], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->fv[k], dims, strides,
+                                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return;
+        }
+    }
+    h->tmap_ready = true;
+}
 
 double *f64(lbm_ctx *h, int k) { return static_cast<double *>(h->fv[k]); }
 float *f32(lbm_ctx *h, int k) { return static_cast<float *>(h->fv[k]); }
@@ -333,6 +383,18 @@ void launch_fused_wstm(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
         h->geof, h->physf, h->mask, src, dst, h->status);
 }
 
+template <bool MASK>
+void launch_fused_wstma(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    using L = lbmf::LatF<1>;
+    const int bytes = (int)sizeof(lbmf::SharedWT<1>);
+    smem_opt_in(lbmf::k_step_f32_wstma<1, MASK>, bytes, done);
+    const lbmf::BoxMaps &tm = h->tmaps[src == h->fv[0] ? 0 : 1];
+    lbmf::k_step_f32_wstma<1, MASK><<<fused_grid<1>(h->geof), 2 * L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, tm, src, dst, h->status);
+}
+
 template <int LAT, bool MASK>
 void launch_fused_ws(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
@@ -376,6 +438,11 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
     if (h->variant == LBM_FUSED_TMEM) {
         if (has_solid(h)) launch_fused_tm<LAT, true>(h, s, src, dst);
         else              launch_fused_tm<LAT, false>(h, s, src, dst);
+        return;
+    }
+    if (LAT == 1 && h->variant == LBM_FUSED_WS_TMA) {   // D3Q27, 32 x 8 tiles, tensor maps made
+        if (has_solid(h)) launch_fused_wstma<true>(h, s, src, dst);
+        else              launch_fused_wstma<false>(h, s, src, dst);
         return;
     }
     if (LAT == 1 && h->variant == LBM_FUSED_WS_TMEM) {   // D3Q27, 32 x 8 tiles
@@ -576,6 +643,8 @@ int read_status(lbm_ctx *h)
     CU(h, cudaStreamSynchronize(h->stream));
     if (st) {
         h->bad = true;
+        if (st & 8)
+            return fail(h, LBM_ECUDA, "the TMA-staged step found its shared memory not 128-byte aligned");
         if (st & 2)
             return fail(h, LBM_ETIMEOUT, "a wait between the fused step's thread groups timed out");
         return fail(h, LBM_ENONFINITE, "a density became non-finite or non-positive");
@@ -1507,12 +1576,13 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     const int variant0 = h->variant;
     int best = h->geof.chunk, best_rows = h->tile_rows, best_variant = h->variant;
     double best_ms = 1e30;
-    for (int var = 0; var <= LBM_FUSED_WS_TMEM && rc == LBM_OK; ++var) {
+    for (int var = 0; var <= LBM_FUSED_WS_TMA && rc == LBM_OK; ++var) {
         if (var > 0 && (h->e64 || (!fp32 && var != LBM_FUSED_TMEM))) continue;
-        if (var == LBM_FUSED_WS_TMEM && h->lattice != LBM_D3Q27) continue;
+        if (var >= LBM_FUSED_WS_TMEM && h->lattice != LBM_D3Q27) continue;
+        if (var == LBM_FUSED_WS_TMA && !h->tmap_ready) continue;
         h->variant = var;
         for (int rows : {8, 7}) {
-            if (rows == 7 && (!two_heights || var == LBM_FUSED_WS_TMEM)) continue;
+            if (rows == 7 && (!two_heights || var >= LBM_FUSED_WS_TMEM)) continue;
             h->tile_rows = rows;
             for (int c : cands) {
                 if (c > nz && c != cands[0]) continue;
@@ -1569,8 +1639,8 @@ int lbm_set_tile(lbm_handle h, int tile_y)
         return fail(h, LBM_EINVAL, "the tile height is a parameter of the D3Q27 FP32 step only");
     if (tile_y != 7 && tile_y != 8) return fail(h, LBM_EINVAL, "tile height must be 7 or 8");
     if (tile_y == 7 && h->e64) return fail(h, LBM_EINVAL, "the FP64-EOS step runs 8-row tiles");
-    if (tile_y == 7 && h->variant == LBM_FUSED_WS_TMEM)
-        return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory form runs 8-row tiles");
+    if (tile_y == 7 && h->variant >= LBM_FUSED_WS_TMEM)
+        return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory forms run 8-row tiles");
     if (h->tile_rows != tile_y && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -1582,15 +1652,19 @@ int lbm_set_tile(lbm_handle h, int tile_y)
 int lbm_set_fused_variant(lbm_handle h, int variant)
 {
     if (!h) return LBM_EINVAL;
-    if (variant < LBM_FUSED_PLAIN || variant > LBM_FUSED_WS_TMEM)
+    if (variant < LBM_FUSED_PLAIN || variant > LBM_FUSED_WS_TMA)
         return fail(h, LBM_EINVAL, "unknown fused-step variant %d", variant);
-    if (variant == LBM_FUSED_WS_TMEM && (h->lattice != LBM_D3Q27 || h->tile_rows != 8))
-        return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory form runs D3Q27 32 x 8 tiles");
+    if (variant >= LBM_FUSED_WS_TMEM && (h->lattice != LBM_D3Q27 || h->tile_rows != 8))
+        return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory forms run D3Q27 32 x 8 tiles");
+    if (variant == LBM_FUSED_WS_TMA &&
+        (h->storage != LBM_F32 || h->geo.nx % 4 || (h->fv[0] && !h->tmap_ready)))
+        return fail(h, LBM_EINVAL, "the TMA-staged form needs FP32 storage, nx a multiple of 4 and the "
+                                   "driver's tensor-map encoder");
     if (h->storage == LBM_F64 && variant != LBM_FUSED_PLAIN)
         return fail(h, LBM_EINVAL, "the FP64 step has one form");
     if (h->e64 && variant != LBM_FUSED_PLAIN)
         return fail(h, LBM_EINVAL, "the FP64-EOS step has one form");
-    if (shifted(h->storage) && (variant == LBM_FUSED_WARP_SPECIALISED || variant == LBM_FUSED_WS_TMEM))
+    if (shifted(h->storage) && (variant == LBM_FUSED_WARP_SPECIALISED || variant >= LBM_FUSED_WS_TMEM))
         return fail(h, LBM_EINVAL, "the warp-specialised forms are forms of the FP32 step only");
     if (h->variant != variant && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);

@@ -21,9 +21,11 @@
 #error "include lbm_fused_f32.cuh or lbm_fused_f32_r7.cuh"
 #endif
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace LBMF_NS {
@@ -206,7 +208,8 @@ template <int LAT> struct SharedF {
     float sg[RS][TY][TX];    // sign of P - P0, interior nodes
     float g[GS][3][GY][GX];  // rho u_a^3
     int xw[AX], yw[AY];      // wrapped halo coordinates
-    float4 uv[4][TY][TX];    // (u_x, u_y, u_z, 1/rho) of the interior nodes, from phase A
+    float4 uv[4][TY][TX];    // (u_x, u_y, u_z, 1/rho) of the interior nodes, from phase A (forms
+                             // without Tensor Memory staging)
     unsigned tmem;           // Tensor Memory base address (k_step_f32_tm)
 };
 
@@ -303,24 +306,30 @@ __device__ __forceinline__ void tmem_dealloc(unsigned base, unsigned ncols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
 }
 
-// Store the first Q of v into this thread's lane at taddr (whole warp), and
+// Store the Q populations f and, in the columns after them, the kTmemExtra
+// values x (when given) into this thread's lane at taddr (whole warp), and
 // wait for the store to complete.
+constexpr int kTmemExtra = 5;   // (u_x, u_y, u_z, 1/rho, sign of P - P0)
+
 template <int Q>
-__device__ __forceinline__ void tmem_store_pop(unsigned taddr, const float *f)
+__device__ __forceinline__ void tmem_store_pop(unsigned taddr, const float *f, const float *x = nullptr)
 {
     constexpr int N = Q <= 16 ? 16 : 32;
+    static_assert(Q + kTmemExtra <= N, "the extra values fit the plane slot");
     unsigned v[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = __float_as_uint(f[i < Q ? i : 0]);
+    for (int i = 0; i < N; ++i)
+        v[i] = __float_as_uint(i < Q ? f[i] : (x && i - Q < kTmemExtra) ? x[i - Q] : f[0]);
     if constexpr (N == 32)
         asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n\ttcgen05.wait::st.sync.aligned;" ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]) : "memory");
     else
         asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};\n\ttcgen05.wait::st.sync.aligned;" ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
 }
 
-// Load Q values of this thread's lane at taddr (whole warp).
+// Load the Q populations of this thread's lane at taddr into f and, when x
+// is given, the kTmemExtra values after them into x (whole warp).
 template <int Q>
-__device__ __forceinline__ void tmem_load_pop(unsigned taddr, float *f)
+__device__ __forceinline__ void tmem_load_pop(unsigned taddr, float *f, float *x = nullptr)
 {
     constexpr int N = Q <= 16 ? 16 : 32;
     unsigned v[N];
@@ -330,6 +339,9 @@ __device__ __forceinline__ void tmem_load_pop(unsigned taddr, float *f)
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]) : "r"(taddr) : "memory");
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = __uint_as_float(v[i]);
+    if (x)
+#pragma unroll
+        for (int k = 0; k < kTmemExtra; ++k) x[k] = __uint_as_float(v[Q + k]);
 }
 
 // Halo node k of a tile, interior nodes first: k < NT is the interior node
@@ -405,15 +417,108 @@ __device__ __forceinline__ TileF tile_setup(const GeoF &g, int bx, int by, int b
 
 // Phase A of iteration pl: plane z0 - 2 + pl enters the rings (ring index
 // pl): (rho, |psi|) on the 2-node halo, rho u_a^3 on the 1-node halo, the sign
-// of P - P0 and (u, 1/rho) of the interior nodes; thread tid of NT. Each
+// of P - P0 and (u, 1/rho) of the interior nodes (in shared memory, or with
+// the node's populations in Tensor Memory: TMX, the warp-specialised Tensor
+// Memory forms); thread tid of NT. Each
 // thread owns up to KA halo nodes and issues all their loads before any
 // arithmetic, for memory-level parallelism.
-template <int LAT, bool MASK, bool TM = false, bool E64 = false, typename ST, typename SM>
+// With BOXED (the TMA-staged form, D3Q27 32 x 8 tiles) the plane's
+// populations on the halo tile are already in shared memory (`box`), and
+// the halo nodes are taken in the order of halo_rc_boxed; a node whose
+// coordinates the box does not hold (a ragged tile's wrapped nodes: the box
+// holds the fill value there) is read from global memory as before.
+//
+// The box of one plane in nine dense TMA boxes (D3Q27 32 x 8 tiles): rows
+// top (y0 - 2, y0 - 1), middle (y0 .. y0 + 7), bottom (y0 + 8, y0 + 9) by
+// columns left (x0 - 4 .. x0 - 1), centre (x0 .. x0 + 31), right (x0 + 32 ..
+// x0 + 35), each [i][row][column] and fetched from its own wrapped origin,
+// so that a tile on the lattice's edge finds its periodic halo there too.
+// Left and right boxes are four columns wide, the narrowest a box with
+// 16-byte aligned rows can be (halo columns x0 - 2, x0 - 1 and x0 + 32,
+// x0 + 33 are its last two and first two). A tiled bulk tensor copy writes
+// shared memory from a 128-byte aligned address, so each box starts on one
+// (the 864-byte corners are padded to 896).
+struct BoxS {
+    static constexpr int Q = 27;
+    alignas(128) float mc[Q][8][32];
+    alignas(128) float tc[Q][2][32];
+    alignas(128) float bc[Q][2][32];
+    alignas(128) float ml[Q][8][4];
+    alignas(128) float mr[Q][8][4];
+    alignas(128) float tl[Q][2][4];
+    alignas(128) float tr[Q][2][4];
+    alignas(128) float bl[Q][2][4];
+    alignas(128) float br[Q][2][4];
+    // bytes the nine copies of one plane deliver (without the padding)
+    static constexpr unsigned BYTES = Q * sizeof(float) * (8 * 32 + 2 * 2 * 32 + 2 * 8 * 4 + 4 * 2 * 4);
+};
+static_assert(offsetof(BoxS, tc) % 128 == 0 && offsetof(BoxS, bc) % 128 == 0 && offsetof(BoxS, ml) % 128 == 0 &&
+                  offsetof(BoxS, mr) % 128 == 0 && offsetof(BoxS, tl) % 128 == 0 &&
+                  offsetof(BoxS, tr) % 128 == 0 && offsetof(BoxS, bl) % 128 == 0 &&
+                  offsetof(BoxS, br) % 128 == 0 && sizeof(BoxS) % 128 == 0,
+              "every box starts on a 128-byte boundary");
+
+// Halo node k of a 32 x 8 tile in the TMA-staged order: interior nodes first
+// (as halo_rc), then the centre columns of the two top and two bottom rows
+// (four warps), the four side columns of the middle rows (one warp) and the
+// four 2 x 2 corners (half a warp), so that each warp reads one kind of box.
+__device__ __forceinline__ void halo_rc_boxed(int k, int &r, int &c)
+{
+    if (k < 256) {
+        r = (k >> 5) + 2;
+        c = (k & 31) + 2;
+        return;
+    }
+    const int m = k - 256;
+    if (m < 128) {   // rows 0, 1 (m < 64) and 10, 11, centre columns
+        const int q = m >> 5;
+        r = q < 2 ? q : q + 8;
+        c = (m & 31) + 2;
+    } else if (m < 160) {   // middle rows, columns 0, 1, 34, 35
+        const int e = m & 3;
+        r = 2 + ((m - 128) >> 2);
+        c = e < 2 ? e : e + 32;
+    } else {   // corners: rows 0, 1, 10, 11 by columns 0, 1, 34, 35
+        const int e = m & 3, q = (m - 160) >> 2;
+        r = q < 2 ? q : q + 8;
+        c = e < 2 ? e : e + 32;
+    }
+}
+
+// Load the 27 populations of halo node (r, c) from the box into v.
+template <typename V>
+__device__ __forceinline__ void load_from_box(const BoxS &b, int r, int c, V &v)
+{
+    const int rc = r < 2 ? 0 : r < 10 ? 1 : 2;   // top, middle, bottom
+    const int cc = c < 2 ? 0 : c < 34 ? 1 : 2;   // left, centre, right
+    const int rr = rc == 0 ? r : rc == 1 ? r - 2 : r - 10;
+    const int xx = cc == 0 ? c + 2 : cc == 1 ? c - 2 : c - 34;
+    if (rc == 1 && cc == 1) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) v[i] = b.mc[i][rr][xx];
+    } else if (cc == 1) {
+        const float *q = rc == 0 ? &b.tc[0][rr][xx] : &b.bc[0][rr][xx];
+#pragma unroll
+        for (int i = 0; i < 27; ++i) v[i] = q[i * 64];
+    } else if (rc == 1) {
+        const float *q = cc == 0 ? &b.ml[0][rr][xx] : &b.mr[0][rr][xx];
+#pragma unroll
+        for (int i = 0; i < 27; ++i) v[i] = q[i * 32];
+    } else {
+        const float *q = rc == 0 ? (cc == 0 ? &b.tl[0][rr][xx] : &b.tr[0][rr][xx])
+                                 : (cc == 0 ? &b.bl[0][rr][xx] : &b.br[0][rr][xx]);
+#pragma unroll
+        for (int i = 0; i < 27; ++i) v[i] = q[i * 8];
+    }
+}
+
+template <int LAT, bool MASK, bool TM = false, bool E64 = false, bool TMX = false, bool BOXED = false,
+          typename ST, typename SM>
 __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
                                         const uint8_t *__restrict__ mask,
                                         const ST *__restrict__ f, SM &sm, const TileF &T,
                                         int pl, int tid, const float *__restrict__ rho_src,
-                                        unsigned tbase = 0)
+                                        unsigned tbase = 0, const BoxS *box = nullptr)
 {
     constexpr bool SHIFT = IsShifted<ST>::value;
     using L = LatF<LAT>;
@@ -435,6 +540,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
     const int rs = pl % RS, gs = pl % GS;
     const bool msk = MASK && g.zsolid[zl];   // the plane holds a solid node
     float fi[KA][Q];
+    float ex[kTmemExtra] = {};   // TMX: (u, 1/rho, sign) of the interior node, kept in Tensor Memory
     unsigned nk[KA];
     bool live[KA], solid[KA];
     if constexpr (SHIFT) load_rho_plane<LAT>(sm, g, rho_src, z0, pl + 2, tid, NT);   // for the next iteration
@@ -443,19 +549,27 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
         const int k = tid + u * NT;
         live[u] = k < AX * AY;
         int r, c;
-        halo_rc<LAT>(live[u] ? k : 0, r, c);
+        if constexpr (BOXED) halo_rc_boxed(live[u] ? k : 0, r, c);
+        else                 halo_rc<LAT>(live[u] ? k : 0, r, c);
         nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
         solid[u] = MASK && live[u] && msk && mask[nk[u]];
         if (live[u] && !solid[u]) {
+            bool in_box = false;
+            if constexpr (BOXED) in_box = sm.xok[c] && sm.yok[r];
+            if (in_box) {
+                if constexpr (BOXED) load_from_box(*box, r, c, fi[u]);
+            } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT, MASK>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
+                for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT, MASK>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
+            }
         }
     }
 #pragma unroll
     for (int u = 0; u < KA; ++u) {
         if (!live[u]) continue;
         int r, c;
-        halo_rc<LAT>(tid + u * NT, r, c);
+        if constexpr (BOXED) halo_rc_boxed(tid + u * NT, r, c);
+        else                 halo_rc<LAT>(tid + u * NT, r, c);
         const bool ring1 = c >= 1 && c < AX - 1 && (!THREE || (r >= 1 && r < AY - 1));
         float rho, d, psi64 = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
         float4 uvk = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -501,16 +615,27 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
             s_g[gs][1][gr][c - 1] = gy;
             s_g[gs][2][gr][c - 1] = gz;
         }
-        const int ir = r - HY, ic = c - 2;
-        if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) {
-            s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
-            sm.uv[pl & 3][ir][ic] = uvk;
+        if constexpr (TMX) {
+            if (u == 0) {   // the interior node (halo node tid < NT)
+                ex[0] = uvk.x;
+                ex[1] = uvk.y;
+                ex[2] = uvk.z;
+                ex[3] = uvk.w;
+                ex[4] = d > 0.0f ? 1.0f : -1.0f;
+            }
+        } else {
+            const int ir = r - HY, ic = c - 2;
+            if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) {
+                s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
+                sm.uv[pl & 3][ir][ic] = uvk;
+            }
         }
     }
-    // the thread's interior node (its halo node tid), for phase B two planes on
+    // the thread's interior node (its halo node tid), for phase B two planes
+    // on: populations, bare velocity, 1/rho and the sign of P - P0
     if constexpr (TM) {
         __syncwarp();   // tcgen05.st is warp-collective: reconverge after the loops
-        tmem_store_pop<Q>(tmem_slot<LAT>(tbase, pl & 3), fi[0]);
+        tmem_store_pop<Q>(tmem_slot<LAT>(tbase, pl & 3), fi[0], TMX ? ex : nullptr);
     }
 }
 
@@ -519,7 +644,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
 // their post-collision populations with halfway bounce-back; thread tid of
 // NT owns node (tid % TX, tid / TX), which the caller has checked to lie in
 // the lattice (a ragged tile's last columns or rows may not).
-template <int LAT, bool MASK, bool TM = false, bool E64 = false, typename ST, typename SM>
+template <int LAT, bool MASK, bool TM = false, bool E64 = false, bool TMX = false, typename ST, typename SM>
 __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
                                         const uint8_t *__restrict__ mask,
                                         const ST *__restrict__ f, ST *__restrict__ fout,
@@ -546,9 +671,10 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
     // the node's own populations: from Tensor Memory, where phase A left them
     // (all lanes of the warp take part), or read again (an L2 hit), first
     float fi[Q];
+    float ex[kTmemExtra] = {};   // TMX: (u, 1/rho, sign) from phase A, through Tensor Memory
     if constexpr (TM) {
         __syncwarp();   // tcgen05.ld is warp-collective
-        tmem_load_pop<Q>(tmem_slot<LAT>(tbase, pc & 3), fi);
+        tmem_load_pop<Q>(tmem_slot<LAT>(tbase, pc & 3), fi, TMX ? ex : nullptr);
         if (!inside) return;
     }
     if (!(MASK && g.zsolid[zc] && mask[n])) {
@@ -559,7 +685,7 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
         const int cr = ty + HY, cc = tx + 2;
         const float2 c0 = s_rp[pc % RS][cr][cc];
         const float rho = c0.x;
-        const float spsi = s_sg[pc % RS][ty][tx] * c0.y;
+        const float spsi = (TMX ? ex[4] : s_sg[pc % RS][ty][tx]) * c0.y;
         if (!(rho > 0.0f) || !isfinite(rho)) atomicOr(status, 1);
         if constexpr (SHIFT) rho_dst[n] = rho;   // source density of what this node pushes
         // Korteweg force (Eq. Kforce_final, sign as the force on the fluid).
@@ -669,7 +795,7 @@ __device__ __forceinline__ void phase_b(const GeoF &g, const PhysF &p,
         Phi[2] = pref * 0.5f *
                  (s_g[(pc + 1) % GS][2][gr0][gc0] - s_g[(pc - 1) % GS][2][gr0][gc0]);
         // bare velocity and 1/rho of the node, formed by phase A from the same populations
-        const float4 uvn = sm.uv[pc & 3][ty][tx];
+        const float4 uvn = TMX ? make_float4(ex[0], ex[1], ex[2], ex[3]) : sm.uv[pc & 3][ty][tx];
         const float inv = uvn.w;
         const float un[3] = {uvn.x, uvn.y, uvn.z};
         // product-form factors, paired (equilibrium, extended)
@@ -836,7 +962,7 @@ __device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
                 break;
             }
             if constexpr (TM) tmem_fence_after();
-            phase_a<LAT, MASK, TM>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase);
+            phase_a<LAT, MASK, TM, false, TM>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase);
             if constexpr (TM) tmem_fence_before();
             mbar_arrive(&sm.full[pl % 6]);
         }
@@ -851,8 +977,8 @@ __device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
             if (pl >= 4) {
                 if constexpr (TM) {
                     tmem_fence_after();
-                    phase_b<LAT, MASK, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr, tbase,
-                                             inside);
+                    phase_b<LAT, MASK, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr,
+                                                          tbase, inside);
                     tmem_fence_before();
                 } else if (inside) {
                     phase_b<LAT, MASK>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr);
@@ -894,6 +1020,192 @@ k_step_f32_wstm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *
     const unsigned tbase = sm.tmem;
     fused_tile_ws<LAT, MASK, true>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm,
                                    tbase);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, COLS);
+}
+
+// ---- TMA staging of the entering planes -------------------------------
+// The warp-specialised producers above spend most of a plane waiting for
+// their own loads (27 per halo node, issued before any arithmetic, then a
+// full memory round trip per plane). Here nine bulk tensor copies per plane
+// (BoxS) move the plane's populations on the tile's halo into shared memory,
+// the populations viewed as a 4D tensor (x, y, z, i), and warp 0 requests
+// each plane's boxes kBoxAhead planes before the producers need them, so
+// phase A reads shared memory. Box stage (pl + kBoxAhead) % kBoxStages held
+// ring index pl - 1: warp 0 requests the boxes of pl + kBoxAhead once
+// full[(pl - 1) % 6] shows every producer past pl - 1.
+constexpr int kBoxStages = 3, kBoxAhead = kBoxStages - 1;
+
+// The four box shapes as tensor maps of one population buffer: 32 x 8,
+// 32 x 2, 4 x 8 and 4 x 2 (x by y), one plane, all 27 populations.
+struct BoxMaps {
+    CUtensorMap mc, tc, ml, tl;
+};
+
+template <int LAT> struct SharedWT : SharedWS<LAT> {
+    alignas(128) BoxS box[kBoxStages];
+    unsigned long long bfull[kBoxStages];
+    // the box holds halo column c / row r (its source coordinate is the
+    // node's wrapped one; false only on ragged tiles)
+    unsigned char xok[SharedF<LAT>::AX], yok[SharedF<LAT>::AY];
+};
+
+// Arm bar for `bytes` more bytes (one arrival).
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\t"
+                 "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Copy the box whose first element is (x, y, z, 0) into dst, completing on
+// bar. x must be a multiple of 4 (16-byte aligned rows).
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, unsigned long long *bar, int x,
+                                            int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int LAT, bool MASK>
+__device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
+                                                 const uint8_t *__restrict__ mask,
+                                                 const float *__restrict__ f, float *__restrict__ fout,
+                                                 int *__restrict__ status, int bx, int by, int bz,
+                                                 SharedWT<LAT> &sm, unsigned tbase, const BoxMaps *maps)
+{
+    constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
+    constexpr int AX = SharedF<LAT>::AX, AY = SharedF<LAT>::AY;
+    static_assert(LAT == 1 && TX == 32 && LatF<LAT>::TY == 8, "the box layout is that of D3Q27 32 x 8 tiles");
+    const int tid = threadIdx.x;
+    const TileF T = tile_setup<LAT, float>(g, bx, by, bz, sm, tid, 2 * NT, nullptr);
+    // box origins: columns x0 - 4, x0, x0 + 32 and rows y0 - 2, y0, y0 + 8, wrapped
+    const int xl = ((T.x0 - 4) % g.nx + g.nx) % g.nx, xr = (T.x0 + 32) % g.nx;
+    const int yt = ((T.y0 - 2) % g.ny + g.ny) % g.ny, yb = (T.y0 + 8) % g.ny;
+    if (tid < AX) {   // (the wrapped coordinates formed here, not read from tile_setup's)
+        const int c = tid;
+        const int xs = c < 2 ? xl + c + 2 : c < 34 ? T.x0 + c - 2 : xr + c - 34;
+        sm.xok[c] = xs < g.nx && xs == ((T.x0 - 2 + c) % g.nx + g.nx) % g.nx;
+    } else if (tid < AX + AY) {
+        const int r = tid - AX;
+        const int ys = r < 2 ? yt + r : r < 10 ? T.y0 + r - 2 : yb + r - 10;
+        sm.yok[r] = ys < g.ny && ys == ((T.y0 - 2 + r) % g.ny + g.ny) % g.ny;
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 6; ++k) {
+            mbar_init(&sm.full[k], NT);
+            mbar_init(&sm.empty[k], NT);
+        }
+        for (int k = 0; k < kBoxStages; ++k) mbar_init(&sm.bfull[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // The boxes' 128-byte alignment rests on that of the dynamic shared
+    // memory's base: a block that finds it otherwise sets bit 3 of the
+    // status and copies nothing (the same for all its threads).
+    if (smem_u32(&sm.box[0]) % 128u) {
+        if (tid == 0) atomicOr(status, 8);
+        return;
+    }
+    // the nine boxes of ring index r (plane z0 - 2 + r) into stage r % kBoxStages
+    auto request = [&](int r) {
+        const int st = r % kBoxStages;
+        BoxS &b = sm.box[st];
+        unsigned long long *bar = &sm.bfull[st];
+        const int z = wrapf(T.z0 - 2 + r, g.nz);
+        mbar_expect_tx(bar, BoxS::BYTES);
+        tma_load_4d(&b.mc[0][0][0], &maps->mc, bar, T.x0, T.y0, z);
+        tma_load_4d(&b.tc[0][0][0], &maps->tc, bar, T.x0, yt, z);
+        tma_load_4d(&b.bc[0][0][0], &maps->tc, bar, T.x0, yb, z);
+        tma_load_4d(&b.ml[0][0][0], &maps->ml, bar, xl, T.y0, z);
+        tma_load_4d(&b.mr[0][0][0], &maps->ml, bar, xr, T.y0, z);
+        tma_load_4d(&b.tl[0][0][0], &maps->tl, bar, xl, yt, z);
+        tma_load_4d(&b.tr[0][0][0], &maps->tl, bar, xr, yt, z);
+        tma_load_4d(&b.bl[0][0][0], &maps->tl, bar, xl, yb, z);
+        tma_load_4d(&b.br[0][0][0], &maps->tl, bar, xr, yb, z);
+    };
+    if (tid < NT) {
+        int issued = 0;   // ring indices whose boxes have been requested (thread 0's count)
+        if (tid == 0)
+            for (; issued < kBoxStages && issued < T.np; ++issued) request(issued);
+        int pl = 0;
+        for (; pl < T.np; ++pl) {
+            if (tid < 32 && pl >= 1 && pl + kBoxAhead < T.np) {
+                const int old = pl - 1;
+                if (!mbar_wait(&sm.full[old % 6], (old / 6) & 1)) {
+                    atomicOr(status, 2);
+                    break;
+                }
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    request(pl + kBoxAhead);
+                    issued = pl + kBoxAhead + 1;
+                }
+                __syncwarp();
+            }
+            if (pl >= 6 && !mbar_wait(&sm.empty[(pl - 2) % 6], ((pl - 6) / 6) & 1)) {
+                atomicOr(status, 2);
+                break;
+            }
+            if (!mbar_wait(&sm.bfull[pl % kBoxStages], (pl / kBoxStages) & 1)) {
+                atomicOr(status, 2);
+                break;
+            }
+            tmem_fence_after();
+            phase_a<LAT, MASK, true, false, true, true>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase,
+                                                        &sm.box[pl % kBoxStages]);
+            tmem_fence_before();
+            mbar_arrive(&sm.full[pl % 6]);
+        }
+        // After a wait ran out, the boxes requested but not yet seen to land
+        // (ring indices pl .. issued - 1, distinct stages) land, each wait
+        // bounded, before the block exits and its shared memory is reused.
+        if (tid == 0)
+            for (int r = pl; r < issued; ++r)
+                if (!mbar_wait(&sm.bfull[r % kBoxStages], (r / kBoxStages) & 1)) break;
+    } else {
+        const int t = tid - NT;
+        const bool inside = T.x0 + t % TX < g.nx && T.y0 + t / TX < g.ny;
+        for (int pl = 0; pl < T.np; ++pl) {
+            if (!mbar_wait(&sm.full[pl % 6], (pl / 6) & 1)) {
+                atomicOr(status, 2);
+                break;
+            }
+            if (pl >= 4) {
+                tmem_fence_after();
+                phase_b<LAT, MASK, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr, tbase,
+                                                      inside);
+                tmem_fence_before();
+                mbar_arrive(&sm.empty[pl % 6]);
+            }
+        }
+    }
+}
+
+// Warp-specialised with Tensor Memory staging and TMA staging of each
+// entering plane's halo (D3Q27 FP32 32 x 8 tiles; nx a multiple of 4, so
+// the tensor's rows are 16-byte aligned); maps are the source population
+// buffer f as a 4D tensor (x, y, z, i) with the four box shapes; dynamic
+// shared memory of sizeof(SharedWT<LAT>).
+template <int LAT, bool MASK>
+__global__ void __launch_bounds__(2 * LatF<LAT>::TX * LatF<LAT>::TY, 1)
+k_step_f32_wstma(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const __grid_constant__ BoxMaps maps,
+                 const float *__restrict__ f, float *__restrict__ fout, int *__restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw128[];
+    SharedWT<LAT> &sm = *reinterpret_cast<SharedWT<LAT> *>(smem_raw128);
+    constexpr unsigned COLS = TmemF<LAT>::COLS;
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned tbase = sm.tmem;
+    fused_tile_wstma<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm, tbase,
+                                &maps);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();

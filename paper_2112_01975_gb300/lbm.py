@@ -18,9 +18,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 D2Q9, D3Q27 = 0, 1
 EOS_VDW, EOS_PR, EOS_RKS, EOS_CS, EOS_SC1, EOS_SC2 = 0, 1, 2, 3, 4, 5
 F64, F32, F16S, BF16S = 0, 1, 2, 3
-FUSED_PLAIN, FUSED_WARP_SPECIALISED, FUSED_TMEM, FUSED_WS_TMEM = 0, 1, 2, 3
+FUSED_PLAIN, FUSED_WARP_SPECIALISED, FUSED_TMEM, FUSED_WS_TMEM, FUSED_WS_TMA = 0, 1, 2, 3, 4
 FUSED_NAMES = {0: "plain", 1: "warp-specialised", 2: "tensor-memory",
-               3: "warp-specialised, tensor-memory"}
+               3: "warp-specialised, tensor-memory",
+               4: "warp-specialised, tensor-memory, TMA-staged planes"}
 FLAG_PHI_OFF = 1
 FLAG_EOS_F64 = 2
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
@@ -303,8 +304,8 @@ class LBM:
         self._check(_lib.lbm_set_tile(self._h, int(tile_y)))
 
     def set_fused_variant(self, variant: int):
-        """Form of the FP32 fused step: FUSED_PLAIN, FUSED_WARP_SPECIALISED
-        or FUSED_TMEM (bitwise the same results)."""
+        """Form of the fused step: FUSED_PLAIN, FUSED_WARP_SPECIALISED,
+        FUSED_TMEM, FUSED_WS_TMEM or FUSED_WS_TMA (bitwise the same results)."""
         self._check(_lib.lbm_set_fused_variant(self._h, int(variant)))
 
     @property

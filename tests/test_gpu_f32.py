@@ -191,6 +191,55 @@ def test_f32_seven_row_tiles_do_not_change_results(lbm, shape, chunk, solid):
     assert np.array_equal(g.get_populations(), f8)
 
 
+@pytest.mark.parametrize("shape,chunk,solid", [((128, 40, 48), 16, True), ((36, 20, 24), 5, True),
+                                              ((96, 64, 33), 1, False)])
+def test_f32_tma_staged_form_is_bitwise_the_plain_form(lbm, shape, chunk, solid):
+    """The TMA-staged form (each entering plane's halo box copied into shared
+    memory two planes ahead; nodes whose halo coordinates wrap read from
+    global memory) gives bitwise the populations of the plain form: tiles
+    whose box lies inside the lattice (128 x 40), ragged tiles that all
+    touch the lattice's edges (36 x 20), chunks of one plane, a solid
+    bottom plane with pillars, graph replays and a plain launch."""
+    w = inputs.DROP_D3Q27_128
+    nx, ny, nz = shape
+    mask = None
+    if solid:
+        mask = inputs.pillar_mask(nx, ny, nz, 2, 4, 6)
+    g = lbm.LBM(1, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b,
+                storage=lbm.F32, mask=mask, rho_w=w.rho_v)
+    g.init(inputs.add_noise(inputs.drop(nx, ny, nz, min(nx, ny, nz) / 4.0, w.rho_v, w.rho_l), 1e-4, 7))
+    g.set_chunk(chunk)
+    g.step(3)
+    f0 = g.get_populations()
+    g.step(9)
+    ref = g.get_populations()
+    g.set_populations(f0)
+    g.set_fused_variant(lbm.FUSED_WS_TMA)
+    assert g.fused_variant == lbm.FUSED_WS_TMA
+    g.step(8)                      # graph replays
+    g.step(1)                      # and a plain launch
+    assert np.array_equal(g.get_populations(), ref)
+
+
+def test_f32_tma_staged_form_rejects_other_cases(lbm):
+    """nx not a multiple of 4 (rows not 16-byte aligned), D2Q9, 7-row tiles
+    and shifted storage have no TMA-staged form."""
+    w = inputs.DROP_D3Q27_128
+    for nx, lattice, storage in ((37, 1, lbm.F32), (64, 0, lbm.F32), (64, 1, lbm.F16S)):
+        g = lbm.LBM(lattice, nx, 16 if lattice else 64, 12 if lattice else 1, w.eos, w.t_over_tc,
+                    w.kappa, w.tau, a=w.a, b=w.b, storage=storage)
+        with pytest.raises(lbm.LBMError):
+            g.set_fused_variant(lbm.FUSED_WS_TMA)
+    g = lbm.LBM(1, 64, 16, 12, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b, storage=lbm.F32)
+    g.set_tile(7)
+    with pytest.raises(lbm.LBMError):
+        g.set_fused_variant(lbm.FUSED_WS_TMA)
+    g.set_tile(8)
+    g.set_fused_variant(lbm.FUSED_WS_TMA)
+    with pytest.raises(lbm.LBMError):
+        g.set_tile(7)
+
+
 def test_f32_tile_setter_rejects_other_cases(lbm):
     w = inputs.DROP_D3Q27_128
     g = lbm.LBM(1, 32, 16, 12, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b, storage=lbm.F32)
@@ -276,13 +325,13 @@ def pillar_oracle():
     return w, n, mask, rho, o
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_f32_pr_pillars_32cubed_1000_steps(lbm, pillar_oracle, variant):
     """The 32^3 pillar case of the FP64 parity tests (a wall with 4x4x6
     pillars, a Peng-Robinson drop above them) in FP32 storage, with each form
-    of the fused step (plain, warp-specialised, Tensor Memory, both), against the
-    FP64 oracle after 1000 steps at the FP32 tolerances; the four forms
-    agree bitwise."""
+    of the fused step (plain, warp-specialised, Tensor Memory, both, and
+    both with TMA-staged planes), against the FP64 oracle after 1000 steps
+    at the FP32 tolerances; the five forms agree bitwise."""
     w, n, mask, rho, o = pillar_oracle
 
     def run(var):
