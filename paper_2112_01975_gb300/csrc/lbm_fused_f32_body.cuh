@@ -539,6 +539,10 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
     const int zl = wrapf(z0 - 2 + pl, g.nz);
     const int rs = pl % RS, gs = pl % GS;
     const bool msk = MASK && g.zsolid[zl];   // the plane holds a solid node
+    // Solid halo nodes: handled inline, or (BOXED) by a pass after the
+    // fluid computation that overwrites what it wrote for them, so that the
+    // main path is the one of a lattice without solids
+    constexpr bool SOLID_INLINE = MASK && !BOXED;
     float fi[KA][Q];
     float ex[kTmemExtra] = {};   // TMX: (u, 1/rho, sign) of the interior node, kept in Tensor Memory
     unsigned nk[KA];
@@ -552,7 +556,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
         if constexpr (BOXED) halo_rc_boxed(live[u] ? k : 0, r, c);
         else                 halo_rc<LAT>(live[u] ? k : 0, r, c);
         nk[u] = (unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl;
-        solid[u] = MASK && live[u] && msk && mask[nk[u]];
+        solid[u] = SOLID_INLINE && live[u] && msk && mask[nk[u]];
         if (live[u] && !solid[u]) {
             bool in_box = false;
             if constexpr (BOXED) in_box = sm.xok[c] && sm.yok[r];
@@ -628,6 +632,25 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
             if (ir >= 0 && ir < TY && ic >= 0 && ic < TX) {
                 s_sg[rs][ir][ic] = d > 0.0f ? 1.0f : -1.0f;
                 sm.uv[pl & 3][ir][ic] = uvk;
+            }
+        }
+    }
+    if constexpr (MASK && BOXED) {
+        // the solid nodes of the plane: the wall's (rho_w, |psi_w|), no rho u^3
+        // (phase B skips solid nodes, so their other values go unread)
+        if (msk) {
+#pragma unroll
+            for (int u = 0; u < KA; ++u) {
+                if (!live[u]) continue;
+                int r, c;
+                halo_rc_boxed(tid + u * NT, r, c);
+                if (!mask[(unsigned)s_xw[c] + (unsigned)g.nx * (unsigned)s_yw[r] + plane * (unsigned)zl]) continue;
+                s_rp[rs][r][c] = f2(p.rho_w, sqrtf(fabsf(p.spsi_w)));
+                if (c >= 1 && c < AX - 1 && r >= 1 && r < AY - 1) {
+                    s_g[gs][0][r - 1][c - 1] = 0.0f;
+                    s_g[gs][1][r - 1][c - 1] = 0.0f;
+                    s_g[gs][2][r - 1][c - 1] = 0.0f;
+                }
             }
         }
     }
@@ -1177,8 +1200,14 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
             }
             if (pl >= 4) {
                 tmem_fence_after();
-                phase_b<LAT, MASK, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr, tbase,
-                                                      inside);
+                // the solid-node code only where a node or one of its
+                // neighbours can be solid (planes zc - 1 .. zc + 1)
+                if (MASK && planes_solid3(g, T.z0 + pl - 4))
+                    phase_b<LAT, true, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr,
+                                                          tbase, inside);
+                else
+                    phase_b<LAT, false, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr,
+                                                           tbase, inside);
                 tmem_fence_before();
                 mbar_arrive(&sm.empty[pl % 6]);
             }
