@@ -1054,11 +1054,16 @@ k_step_f32_wstm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *
 // their own loads (27 per halo node, issued before any arithmetic, then a
 // full memory round trip per plane). Here nine bulk tensor copies per plane
 // (BoxS) move the plane's populations on the tile's halo into shared memory,
-// the populations viewed as a 4D tensor (x, y, z, i), and warp 0 requests
-// each plane's boxes kBoxAhead planes before the producers need them, so
-// phase A reads shared memory. Box stage (pl + kBoxAhead) % kBoxStages held
-// ring index pl - 1: warp 0 requests the boxes of pl + kBoxAhead once
-// full[(pl - 1) % 6] shows every producer past pl - 1.
+// the populations viewed as a 4D tensor (x, y, z, i), and one producer warp
+// requests each plane's boxes kBoxAhead planes before the producers need
+// them, so phase A reads shared memory. Box stage (pl + kBoxAhead) %
+// kBoxStages held ring index pl - 1: the requesting warp asks for the boxes
+// of pl + kBoxAhead once full[(pl - 1) % 6] shows every producer past
+// pl - 1. Issuing nine copies takes that warp over a thousand cycles per
+// plane, so it is the last producer warp, whose halo share is empty (its
+// threads form only their interior nodes): the wait and the issue fall in
+// time it would otherwise spend waiting for the consumers.
+constexpr int kBoxWarp = 7;
 constexpr int kBoxStages = 3, kBoxAhead = kBoxStages - 1;
 
 // The four box shapes as tensor maps of one population buffer: 32 x 8,
@@ -1151,19 +1156,22 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
         tma_load_4d(&b.bl[0][0][0], &maps->tl, bar, xl, yb, z);
         tma_load_4d(&b.br[0][0][0], &maps->tl, bar, xr, yb, z);
     };
+    static_assert(kBoxWarp * 32 >= (SharedF<LAT>::AX * SharedF<LAT>::AY - NT) && kBoxWarp * 32 < NT,
+                  "the requesting warp has no halo node beyond its interior one");
+    const bool boxer = tid >> 5 == kBoxWarp, boxer0 = tid == kBoxWarp * 32;
     if (tid < NT) {
-        int issued = 0;   // ring indices whose boxes have been requested (thread 0's count)
-        if (tid == 0)
+        int issued = 0;   // ring indices whose boxes have been requested (lane 0 of kBoxWarp's count)
+        if (boxer0)
             for (; issued < kBoxStages && issued < T.np; ++issued) request(issued);
         int pl = 0;
         for (; pl < T.np; ++pl) {
-            if (tid < 32 && pl >= 1 && pl + kBoxAhead < T.np) {
+            if (boxer && pl >= 1 && pl + kBoxAhead < T.np) {
                 const int old = pl - 1;
                 if (!mbar_wait(&sm.full[old % 6], (old / 6) & 1)) {
                     atomicOr(status, 2);
                     break;
                 }
-                if (tid == 0) {
+                if (boxer0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     request(pl + kBoxAhead);
                     issued = pl + kBoxAhead + 1;
@@ -1187,7 +1195,7 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
         // After a wait ran out, the boxes requested but not yet seen to land
         // (ring indices pl .. issued - 1, distinct stages) land, each wait
         // bounded, before the block exits and its shared memory is reused.
-        if (tid == 0)
+        if (boxer0)
             for (int r = pl; r < issued; ++r)
                 if (!mbar_wait(&sm.bfull[r % kBoxStages], (r / kBoxStages) & 1)) break;
     } else {
