@@ -60,11 +60,11 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (an FMA-chain probe measured
 # tile rows, fused-step form); each entry records the SHA-256 prefix of the fused kernel's
 # source it was taken on, and is not used once that source has changed.
 MEASURED_TRAFFIC = {
-    # k_step_f32_wstm, 32 x 8 tiles, chunk 128, on the impact scaled to
-    # 192x192x256: 1091.4 + 966.2 MB for 9,437,184 nodes
-    # (profiles/k_step_f32_wstm_d3q27_impact_192x192x256.md)
-    ("d3q27_impact_384x384x256_pr_tr0.5", "f32", 8, 3): {
-        "bytes_per_node": 218.04, "src_sha": "af9a5b1d17d0e806"},
+    # k_step_f32_wstma, 32 x 8 tiles, chunk 256, on the impact scaled to
+    # 192x192x256: 1069.2 + 960.6 MB for 9,437,184 nodes
+    # (profiles/k_step_f32_wstma_d3q27_impact_192x192x256.md)
+    ("d3q27_impact_384x384x256_pr_tr0.5", "f32", 8, 4): {
+        "bytes_per_node": 215.08, "src_sha": "33968f18fcdd6809"},
 }
 FUSED_SRC = os.path.join(ROOT, "paper_2112_01975_gb300", "csrc", "lbm_fused_f32_body.cuh")
 

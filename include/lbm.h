@@ -252,7 +252,8 @@ int lbm_time_kernels(lbm_handle h, int64_t n, double *ms);
  * results do not depend on it. */
 int lbm_set_chunk(lbm_handle h, int chunk);
 
-/* Pick the chunk of the fused FP32 step by timing candidates on the
+/* Pick the chunk of the fused FP32 step by timing candidates (4 to 128
+ * planes, and the whole march axis when it is longer) on the
  * handle's own state (saved to a temporary device buffer and restored
  * afterwards, so the state is unchanged). Sets and returns it in
  * *chunk_out (0 for FP64 storage, which has no tile parameter). With

@@ -1565,8 +1565,9 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     if (rbytes)
         CU(h, cudaMemcpyAsync(static_cast<char *>(save) + bytes, h->rs[h->cur], rbytes,
                               cudaMemcpyDeviceToDevice, h->stream));
-    const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128};
     const int nz = h->geof.nz;
+    // plane chunks per CTA; the last, the whole march axis (one chunk per column)
+    const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128, nz > 128 ? nz : 128};
     const int chunk0 = h->geof.chunk, rows0 = h->tile_rows;   // restored on failure
     // FP32: the plain, warp-specialised and Tensor Memory kernels; D3Q27 FP32
     // also 32 x 8 and 32 x 7 tiles (the shifted and batched steps use plain
@@ -1584,8 +1585,9 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
         for (int rows : {8, 7}) {
             if (rows == 7 && (!two_heights || var >= LBM_FUSED_WS_TMEM)) continue;
             h->tile_rows = rows;
-            for (int c : cands) {
-                if (c > nz && c != cands[0]) continue;
+            for (int j = 0; j < (int)(sizeof cands / sizeof cands[0]); ++j) {
+                const int c = cands[j];
+                if ((c > nz && j != 0) || (j > 0 && c == cands[j - 1])) continue;
                 h->geof.chunk = c;
                 double ms[2];
                 rc = lbm_time_kernels(h, 1, ms);                  // warm-up
