@@ -240,6 +240,15 @@ int lbm_sync(lbm_handle h, int timeout_ms);
  * each kernel in the graph). */
 int64_t lbm_launch_count(lbm_handle h);
 
+/* Measured FP64 rate of the current device: a grid of 8 blocks of 256
+ * threads per SM runs eight independent FP64 fused multiply-add chains per
+ * thread; *tflops = the best of three launches' 2 x FMAs / duration (CUDA
+ * events), in TFLOP/s. The denominator for the FP64 step's ALU roofline,
+ * measured on the machine that runs it. Allocates and frees a small device
+ * buffer; synchronising. LBM_EINVAL for a null pointer, LBM_ECUDA (or
+ * LBM_ENOMEM) if a CUDA call fails. */
+int lbm_probe_fp64_tflops(double *tflops);
+
 /* Advance n >= 1 steps with plain launches, timing each kernel with CUDA
  * events on the handle's stream. ms[0] receives the mean duration of the
  * moments kernel, ms[1] of the collide-and-stream kernel (milliseconds);
@@ -280,8 +289,9 @@ int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y);
 int lbm_set_tile(lbm_handle h, int tile_y);
 
 /* Forms of the fused step of the reduced storages (LBM_F32; LBM_F16S and
- * LBM_BF16S have the plain and the Tensor Memory form); the same arithmetic
- * in the same order, so results are bitwise the same whichever runs.
+ * LBM_BF16S have the plain, the Tensor Memory and, for D3Q27, the
+ * warp-specialised Tensor Memory form); the same arithmetic in the same
+ * order, so results are bitwise the same whichever runs.
  *   LBM_FUSED_PLAIN (default): one thread group per tile; each entering
  *     plane's densities, pseudo-potentials and velocities are formed, the
  *     block synchronises, and the plane two behind collides and streams,
@@ -304,9 +314,10 @@ enum {
     LBM_FUSED_WS_TMA = 4
 };
 
-/*   LBM_FUSED_WS_TMEM (D3Q27 FP32, 32 x 8 tiles): the warp-specialised form
- *     with the Tensor Memory staging, the producer that loads a node leaving
- *     its populations in the lane of the consumer that collides it.
+/*   LBM_FUSED_WS_TMEM (D3Q27, 32 x 8 tiles; FP32 or shifted storage): the
+ *     warp-specialised form with the Tensor Memory staging, the producer that
+ *     loads a node leaving its populations in the lane of the consumer that
+ *     collides it.
  *   LBM_FUSED_WS_TMA (D3Q27 FP32, 32 x 8 tiles, nx a multiple of 4): the
  *     LBM_FUSED_WS_TMEM form with each entering plane's populations on the
  *     tile's halo copied into shared memory by the tensor-memory-access unit
@@ -317,8 +328,9 @@ enum {
  *     form runs LBM_FUSED_WS_TMEM (lbm_get_fused_variant says which).
  * Select a form of the fused step (lbm_autotune times the forms the
  * storage has). LBM_EINVAL for an unknown form, a form other than
- * LBM_FUSED_PLAIN with LBM_F64 storage or LBM_FLAG_EOS_F64, or the
- * warp-specialised forms with shifted storage, or LBM_FUSED_WS_TMEM or
+ * LBM_FUSED_PLAIN with LBM_F64 storage or LBM_FLAG_EOS_F64, or
+ * LBM_FUSED_WARP_SPECIALISED or LBM_FUSED_WS_TMA with shifted storage, or
+ * LBM_FUSED_WS_TMEM or
  * LBM_FUSED_WS_TMA with D2Q9 or 7-row tiles, or LBM_FUSED_WS_TMA with nx not a
  * multiple of 4 or, after the memory is laid out, without tensor maps. */
 int lbm_set_fused_variant(lbm_handle h, int variant);

@@ -489,11 +489,24 @@ void launch_shifted_tm(lbm_ctx *h, cudaStream_t s, int k)
         h->rs[k], h->rs[k ^ 1], h->status);
 }
 
+template <typename ST, bool MASK>
+void launch_shifted_wstm(lbm_ctx *h, cudaStream_t s, int k)
+{
+    static std::atomic<unsigned long long> done{0};   // devices already opted in
+    const int bytes = (int)sizeof(lbmf::SharedSWS<1>);
+    smem_opt_in(lbmf::k_step_shifted_wstm<1, ST, MASK>, bytes, done);
+    using L = lbmf::LatF<1>;
+    lbmf::k_step_shifted_wstm<1, ST, MASK><<<fused_grid<1>(h->geof), 2 * L::TX * L::TY, bytes, s>>>(
+        h->geof, h->physf, h->mask, static_cast<const ST *>(h->fv[k]), static_cast<ST *>(h->fv[k ^ 1]),
+        h->rs[k], h->rs[k ^ 1], h->status);
+}
+
 template <int LAT, typename ST, bool MASK>
 void launch_shifted_m(lbm_ctx *h, cudaStream_t s, int k)
 {
     if (h->e64) launch_shifted_e<LAT, ST, true, MASK>(h, s, k);
     else if (h->variant == LBM_FUSED_TMEM) launch_shifted_tm<LAT, ST, MASK>(h, s, k);
+    else if (LAT == 1 && h->variant == LBM_FUSED_WS_TMEM) launch_shifted_wstm<ST, MASK>(h, s, k);
     else launch_shifted_e<LAT, ST, false, MASK>(h, s, k);
 }
 
@@ -1272,6 +1285,45 @@ int lbm_sync(lbm_handle h, int timeout_ms)
 
 int64_t lbm_launch_count(lbm_handle h) { return h ? h->launches : -1; }
 
+int lbm_probe_fp64_tflops(double *tflops)
+{
+    if (!tflops) return LBM_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ECUDA;
+    }
+    const int threads = 256, blocks = 8 * sms, iters = 4096;
+    double *out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * threads * blocks) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LBM_OK;
+    double best = 0.0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = LBM_ECUDA;
+    for (int rep = 0; rep < 4 && rc == LBM_OK; ++rep) {   // the first launch warms up
+        cudaEventRecord(e0, 0);
+        lbmk::k_fp64_fma_probe<<<blocks, threads>>>(out, iters);
+        cudaEventRecord(e1, 0);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = LBM_ECUDA;
+            break;
+        }
+        const double tf = 2.0 * 8.0 * iters * (double)threads * blocks / (ms * 1e-3) / 1e12;
+        if (rep > 0 && tf > best) best = tf;
+    }
+    if (rc != LBM_OK) cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (rc == LBM_OK) *tflops = best;
+    return rc;
+}
+
 }  // extern "C"
 
 struct lbm_batch_ctx {
@@ -1578,7 +1630,8 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     int best = h->geof.chunk, best_rows = h->tile_rows, best_variant = h->variant;
     double best_ms = 1e30;
     for (int var = 0; var <= LBM_FUSED_WS_TMA && rc == LBM_OK; ++var) {
-        if (var > 0 && (h->e64 || (!fp32 && var != LBM_FUSED_TMEM))) continue;
+        // shifted storage: plain, Tensor Memory and (D3Q27) warp-specialised Tensor Memory
+        if (var > 0 && (h->e64 || (!fp32 && var != LBM_FUSED_TMEM && var != LBM_FUSED_WS_TMEM))) continue;
         if (var >= LBM_FUSED_WS_TMEM && h->lattice != LBM_D3Q27) continue;
         if (var == LBM_FUSED_WS_TMA && !h->tmap_ready) continue;
         h->variant = var;
@@ -1666,8 +1719,8 @@ int lbm_set_fused_variant(lbm_handle h, int variant)
         return fail(h, LBM_EINVAL, "the FP64 step has one form");
     if (h->e64 && variant != LBM_FUSED_PLAIN)
         return fail(h, LBM_EINVAL, "the FP64-EOS step has one form");
-    if (shifted(h->storage) && (variant == LBM_FUSED_WARP_SPECIALISED || variant >= LBM_FUSED_WS_TMEM))
-        return fail(h, LBM_EINVAL, "the warp-specialised forms are forms of the FP32 step only");
+    if (shifted(h->storage) && (variant == LBM_FUSED_WARP_SPECIALISED || variant == LBM_FUSED_WS_TMA))
+        return fail(h, LBM_EINVAL, "shifted storage has the plain and the two Tensor Memory forms");
     if (h->variant != variant && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;

@@ -928,6 +928,13 @@ template <int LAT> struct SharedWS : SharedF<LAT> {
     unsigned long long full[6], empty[6];
 };
 
+// The same with the source-density ring of shifted 16-bit storage, and two
+// producer-only barriers (pbar[pl % 2] completes when every producer has
+// finished iteration pl, its source-density plane included).
+template <int LAT> struct SharedSWS : SharedS<LAT> {
+    unsigned long long full[6], empty[6], pbar[2];
+};
+
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -958,22 +965,37 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     }
 }
 
-template <int LAT, bool MASK, bool TM = false>
+// Shifted storage (ST 16-bit, SM = SharedSWS): the producers also keep the
+// source-density ring, which only they read (the consumers take the decoded
+// populations from Tensor Memory: TM), and wait for one another once per
+// plane (pbar, bounded like the other waits) so that the plane one producer
+// loads is in place before another decodes with it. Producer iteration pl
+// waits for pbar[(pl - 1) % 2]'s completion of iteration pl - 1; the next
+// arrival on that barrier (iteration pl + 1) comes from a producer that has
+// seen iteration pl complete, so after every producer's wait: parity exact.
+template <int LAT, bool MASK, bool TM = false, typename ST = float, typename SM = SharedWS<LAT>>
 __device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
                                               const uint8_t *__restrict__ mask,
-                                              const float *__restrict__ f, float *__restrict__ fout,
+                                              const ST *__restrict__ f, ST *__restrict__ fout,
                                               int *__restrict__ status, int bx, int by, int bz,
-                                              SharedWS<LAT> &sm, unsigned tbase = 0)
+                                              SM &sm, unsigned tbase = 0,
+                                              const float *__restrict__ rho_src = nullptr,
+                                              float *__restrict__ rho_dst = nullptr)
 {
+    constexpr bool SHIFT = IsShifted<ST>::value;
     constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
     static_assert(!TM || NT % 256 == 0, "a consumer warp shares its producer's Tensor Memory lanes");
+    static_assert(!SHIFT || TM, "shifted storage hands the decoded populations over in Tensor Memory");
     const int tid = threadIdx.x;
-    const TileF T = tile_setup<LAT, float>(g, bx, by, bz, sm, tid, 2 * NT, nullptr);
-    if (tid == 0)
+    const TileF T = tile_setup<LAT, ST>(g, bx, by, bz, sm, tid, 2 * NT, rho_src);
+    if (tid == 0) {
         for (int k = 0; k < 6; ++k) {
             mbar_init(&sm.full[k], NT);
             mbar_init(&sm.empty[k], NT);
         }
+        if constexpr (SHIFT)
+            for (int k = 0; k < 2; ++k) mbar_init(&sm.pbar[k], NT);
+    }
     __syncthreads();
     // A wait that runs out sets bit 2 of the status and ends this group's
     // loop; the other group's next wait then runs out too, so every thread
@@ -984,9 +1006,16 @@ __device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
                 atomicOr(status, 2);
                 break;
             }
+            if constexpr (SHIFT) {   // the source densities loaded in iteration pl - 1 are in place
+                if (pl > 0 && !mbar_wait(&sm.pbar[(pl - 1) & 1], ((pl - 1) >> 1) & 1)) {
+                    atomicOr(status, 2);
+                    break;
+                }
+            }
             if constexpr (TM) tmem_fence_after();
-            phase_a<LAT, MASK, TM, false, TM>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase);
+            phase_a<LAT, MASK, TM, false, TM>(g, p, mask, f, sm, T, pl, tid, rho_src, tbase);
             if constexpr (TM) tmem_fence_before();
+            if constexpr (SHIFT) mbar_arrive(&sm.pbar[pl & 1]);
             mbar_arrive(&sm.full[pl % 6]);
         }
     } else {
@@ -1000,7 +1029,7 @@ __device__ __forceinline__ void fused_tile_ws(const GeoF &g, const PhysF &p,
             if (pl >= 4) {
                 if constexpr (TM) {
                     tmem_fence_after();
-                    phase_b<LAT, MASK, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr,
+                    phase_b<LAT, MASK, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, rho_dst,
                                                           tbase, inside);
                     tmem_fence_before();
                 } else if (inside) {
@@ -1320,6 +1349,31 @@ k_step_shifted_tm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const ST *_
     const unsigned tbase = sm.tmem;
     fused_tile<LAT, MASK, ST, SharedS<LAT>, true>(g, p, mask, f, fout, status, blockIdx.x,
                                                   blockIdx.y, blockIdx.z, sm, rho_src, rho_dst, tbase);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, COLS);
+}
+
+// Shifted 16-bit storage, warp-specialised with the decoded populations
+// handed from producer to consumer in Tensor Memory (D3Q27 32 x 8 tiles, as
+// k_step_f32_wstm); dynamic shared memory of sizeof(SharedSWS<LAT>).
+template <int LAT, typename ST, bool MASK>
+__global__ void __launch_bounds__(2 * LatF<LAT>::TX * LatF<LAT>::TY, 1)
+k_step_shifted_wstm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const ST *__restrict__ f,
+                    ST *__restrict__ fout, const float *__restrict__ rho_src, float *__restrict__ rho_dst,
+                    int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedSWS<LAT> &sm = *reinterpret_cast<SharedSWS<LAT> *>(smem_raw);
+    constexpr unsigned COLS = TmemF<LAT>::COLS;
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned tbase = sm.tmem;
+    fused_tile_ws<LAT, MASK, true, ST, SharedSWS<LAT>>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y,
+                                                       blockIdx.z, sm, tbase, rho_src, rho_dst);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();

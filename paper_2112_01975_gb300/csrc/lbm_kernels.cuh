@@ -641,4 +641,23 @@ __global__ void k_convert(size_t n, const A *__restrict__ in, B *__restrict__ ou
         out[k] = (B)in[k];
 }
 
+// FP64 throughput probe: eight independent fused multiply-add chains per
+// thread (two flops each), iters rounds, the chains' sum stored so that none
+// is eliminated. a -> a b + c with b = 1 - 2^-20 and c = 2^-20 stays near 1
+// (no overflow, no subnormals).
+__global__ void k_fp64_fma_probe(double *__restrict__ out, int iters)
+{
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    const double b = 1.0 - 0x1p-20, c = 0x1p-20;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace lbmk

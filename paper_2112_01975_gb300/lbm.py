@@ -64,6 +64,7 @@ def _load():
     L.lbm_sync.argtypes = [vp, C.c_int]
     L.lbm_launch_count.restype = i64
     L.lbm_launch_count.argtypes = [vp]
+    L.lbm_probe_fp64_tflops.argtypes = [dp]
     L.lbm_time_kernels.argtypes = [vp, i64, dp]
     L.lbm_set_chunk.argtypes = [vp, C.c_int]
     L.lbm_autotune.argtypes = [vp, C.POINTER(C.c_int)]
@@ -116,6 +117,16 @@ lbm_batch_launch_count = _lib.lbm_batch_launch_count
 lbm_batch_destroy = _lib.lbm_batch_destroy
 lbm_last_error = _lib.lbm_last_error
 lbm_destroy = _lib.lbm_destroy
+
+
+def probe_fp64_tflops() -> float:
+    """Measured FP64 rate of the current device in TFLOP/s (an FMA-chain
+    probe; the denominator of the FP64 step's ALU roofline)."""
+    v = C.c_double()
+    rc = _lib.lbm_probe_fp64_tflops(C.byref(v))
+    if rc:
+        raise LBMError(rc, "FP64 probe failed")
+    return v.value
 
 
 def default_params(eos: int) -> lbm_params:

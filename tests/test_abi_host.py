@@ -95,6 +95,7 @@ def test_null_handle_calls_are_errors(lib):
     on = C.c_int(-1)
     assert lib.lbm_set_fused_variant(None, 1) == 1
     assert lib.lbm_get_fused_variant(None, C.byref(on)) == 1 and on.value == -1
+    assert lib.lbm_probe_fp64_tflops(None) == 1
     lib.lbm_last_error.restype = C.c_char_p
     assert lib.lbm_last_error(None) == b"null handle"
     lib.lbm_destroy(None)

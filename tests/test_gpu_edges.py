@@ -80,3 +80,13 @@ def test_uniform_state_at_rest_stays(lbm, storage, tol):
     assert np.max(np.abs(f1 - f0)) <= tol * np.max(np.abs(f0))
     m, j = g.reduce()
     assert np.all(np.abs(j) < 1e-9 * m)
+
+
+def test_fp64_probe_measures_a_plausible_rate(lbm):
+    """The FP64 FMA-chain probe (the FP64 roofline's denominator) reports a
+    rate between a tenth and three times GB300's nominal 1.25 TFLOP/s, and
+    two runs agree within 10 %."""
+    a = lbm.probe_fp64_tflops()
+    b = lbm.probe_fp64_tflops()
+    assert 0.125 < a < 3.75, a
+    assert abs(a - b) < 0.1 * max(a, b), (a, b)

@@ -124,21 +124,23 @@ def test_shifted_mass_drift_and_io(lbm, storage):
 @pytest.mark.parametrize("storage", [2, 3])
 @pytest.mark.parametrize("lattice", [0, 1])
 def test_shifted_tensor_memory_form_is_bitwise_the_plain_one(lbm, storage, lattice):
-    """The Tensor Memory form of the shifted step (each node's decoded
-    populations kept between the phases) against the plain form, on ragged
-    lattices: bitwise the same after 40 steps."""
+    """The Tensor Memory forms of the shifted step (each node's decoded
+    populations kept between the phases; on D3Q27 also the warp-specialised
+    one, whose producers share the source-density ring) against the plain
+    form, on ragged lattices: bitwise the same after 40 steps."""
     w = inputs.DROP_D3Q27_128 if lattice else inputs.DROP_D2Q9_64
     nx, ny, nz = (45, 37, 30) if lattice else (150, 70, 1)
     rho = inputs.add_noise(inputs.drop(nx, ny, nz, 9.0, w.rho_v, w.rho_l), 1e-4, 17)
     out = []
-    for variant in (0, 2):
+    for variant in ((0, 2, 3) if lattice else (0, 2)):
         g = lbm.LBM(lattice, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, 0.8, a=w.a, b=w.b,
                     storage=storage)
         g.set_fused_variant(variant)
         g.init(rho)
         g.step(40)
         out.append(g.get_populations())
-    assert np.array_equal(out[0], out[1])
+    for x in out[1:]:
+        assert np.array_equal(out[0], x)
 
 
 @pytest.mark.parametrize("storage", [2, 3])
@@ -147,8 +149,8 @@ def test_shifted_storage_with_solid_nodes(lbm, storage):
     pillar case: a wall with 4x4x6 pillars under a Peng-Robinson drop): a
     population bounced back by a node is stored relative to that node's own
     density. Against the FP64 oracle after 500 steps at the storage's
-    tolerance, mass conserved to 1e-4, and the plain and Tensor Memory forms
-    bitwise equal."""
+    tolerance, mass conserved to 1e-4, and the plain and the two Tensor
+    Memory forms bitwise equal."""
     from test_gpu_parity import _pillar_case
     w, n, mask, rho = _pillar_case()
     try:   # the -fopenmp build: bitwise the plain oracle, on all host cores
@@ -160,7 +162,7 @@ def test_shifted_storage_with_solid_nodes(lbm, storage):
     o.init(rho)
     o.step(500)
     pops = []
-    for variant in (0, 2):
+    for variant in (0, 2, 3):
         g = lbm.LBM(1, n, n, n, w.eos, w.t_over_tc, w.kappa, 0.8, mask=mask, a=w.a, b=w.b,
                     rho_w=w.rho_v, storage=storage)
         g.set_fused_variant(variant)
@@ -174,4 +176,4 @@ def test_shifted_storage_with_solid_nodes(lbm, storage):
         fl = mask == 0
         assert np.max(np.abs(rg[fl] - ro[fl]) / ro[fl]) < TOL
         pops.append(g.get_populations())
-    assert np.array_equal(pops[0], pops[1])
+    assert np.array_equal(pops[0], pops[1]) and np.array_equal(pops[0], pops[2])
