@@ -249,6 +249,17 @@ int64_t lbm_launch_count(lbm_handle h);
  * LBM_ENOMEM) if a CUDA call fails. */
 int lbm_probe_fp64_tflops(double *tflops);
 
+/* Self-test of the fused kernels' bounded waits on the current device: one
+ * block of 64 threads waits, through the same wait function, for an
+ * mbarrier phase that no thread ever completes; each warp gives up after
+ * limit_cycles (1 .. 2e9) SM clock cycles and sets bit 2 of a status word,
+ * as a timed-out wait in a step does. *status_bits = that word (2 when the
+ * waits ran out and returned), *ms = the launch's duration. No fault, trap
+ * or hang is involved: the kernel returns by itself and the context stays
+ * usable. LBM_EINVAL for null pointers or a limit out of range, LBM_ECUDA
+ * (or LBM_ENOMEM) if a CUDA call fails; synchronising. */
+int lbm_selftest_wait_timeout(long long limit_cycles, int *status_bits, double *ms);
+
 /* Advance n >= 1 steps with plain launches, timing each kernel with CUDA
  * events on the handle's stream. ms[0] receives the mean duration of the
  * moments kernel, ms[1] of the collide-and-stream kernel (milliseconds);

@@ -1,7 +1,8 @@
 """Build the CUDA library ``_build/liblbm.so`` for sm_103a with nvcc.
 
-Two translation units (the C ABI with its kernels, and the allocation-free
-reduction), one -gencode, in-tree output.
+Three translation units (the C ABI with its kernels, the TMA-staged step's
+instantiations, and the allocation-free reduction), compiled in parallel
+to objects and linked; one -gencode, in-tree output.
 """
 from __future__ import annotations
 
@@ -16,8 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
-SOURCES = [os.path.join(CSRC, "lbm_api.cu"), os.path.join(CSRC, "lbm_noalloc.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + \
+SOURCES = [os.path.join(CSRC, "lbm_api.cu"), os.path.join(CSRC, "lbm_step_tma.cu"),
+           os.path.join(CSRC, "lbm_noalloc.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(INCLUDE, "lbm.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -41,9 +43,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if all(os.path.getmtime(d) <= t for d in DEPS):
             return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc(), "-shared", *flags(["-Xptxas", "-v"] if verbose else []), "-o", tmp, *SOURCES]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    extra = ["-Xptxas", "-v"] if verbose else []
+    objs = [os.path.join(OUT_DIR, os.path.basename(src) + ".%d.o" % os.getpid()) for src in SOURCES]
+    procs = [subprocess.Popen([nvcc(), "-c", *flags(extra), "-o", obj, src])
+             for src, obj in zip(SOURCES, objs)]
+    failed = [src for src, pr in zip(SOURCES, procs) if pr.wait() != 0]
+    try:
+        if failed:
+            raise subprocess.CalledProcessError(1, "nvcc -c " + " ".join(failed))
+        subprocess.run([nvcc(), "-shared", ARCH, "-o", tmp, *objs], check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return LIB
 
 

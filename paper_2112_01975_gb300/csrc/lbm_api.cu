@@ -17,6 +17,7 @@
 #include "lbm_fused_f32.cuh"
 #include "lbm_fused_f32_r7.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_step_tma.h"
 
 using lbmk::Geo;
 using lbmk::Phys;
@@ -383,18 +384,6 @@ void launch_fused_wstm(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
         h->geof, h->physf, h->mask, src, dst, h->status);
 }
 
-template <bool MASK>
-void launch_fused_wstma(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
-{
-    static std::atomic<unsigned long long> done{0};   // devices already opted in
-    using L = lbmf::LatF<1>;
-    const int bytes = (int)sizeof(lbmf::SharedWT<1>);
-    smem_opt_in(lbmf::k_step_f32_wstma<1, MASK>, bytes, done);
-    const lbmf::BoxMaps &tm = h->tmaps[src == h->fv[0] ? 0 : 1];
-    lbmf::k_step_f32_wstma<1, MASK><<<fused_grid<1>(h->geof), 2 * L::TX * L::TY, bytes, s>>>(
-        h->geof, h->physf, h->mask, tm, src, dst, h->status);
-}
-
 template <int LAT, bool MASK>
 void launch_fused_ws(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
 {
@@ -441,8 +430,8 @@ void launch_fused(lbm_ctx *h, cudaStream_t s, const float *src, float *dst)
         return;
     }
     if (LAT == 1 && h->variant == LBM_FUSED_WS_TMA) {   // D3Q27, 32 x 8 tiles, tensor maps made
-        if (has_solid(h)) launch_fused_wstma<true>(h, s, src, dst);
-        else              launch_fused_wstma<false>(h, s, src, dst);
+        lbmtma::launch(h->geof, h->physf, h->mask, h->tmaps[src == h->fv[0] ? 0 : 1], src, dst, h->status,
+                       has_solid(h), s);
         return;
     }
     if (LAT == 1 && h->variant == LBM_FUSED_WS_TMEM) {   // D3Q27, 32 x 8 tiles
@@ -1284,6 +1273,39 @@ int lbm_sync(lbm_handle h, int timeout_ms)
 }
 
 int64_t lbm_launch_count(lbm_handle h) { return h ? h->launches : -1; }
+
+int lbm_selftest_wait_timeout(long long limit_cycles, int *status_bits, double *ms)
+{
+    if (!status_bits || !ms || limit_cycles < 1 || limit_cycles > 2000000000ll) return LBM_EINVAL;
+    int *st = nullptr;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LBM_OK, host = 0;
+    float t = 0.0f;
+    if (cudaMemset(st, 0, sizeof(int)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        rc = LBM_ECUDA;
+    if (rc == LBM_OK) {
+        cudaEventRecord(e0, 0);
+        lbmf::k_wait_selftest<<<1, 64>>>(st, limit_cycles);
+        cudaEventRecord(e1, 0);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess ||
+            cudaMemcpy(&host, st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = LBM_ECUDA;
+    }
+    if (rc != LBM_OK) cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(st);
+    if (rc == LBM_OK) {
+        *status_bits = host;
+        *ms = t;
+    }
+    return rc;
+}
 
 int lbm_probe_fp64_tflops(double *tflops)
 {

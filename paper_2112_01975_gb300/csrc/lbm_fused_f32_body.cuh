@@ -113,13 +113,16 @@ template <int LAT> __device__ __forceinline__ constexpr float weight_f(int i)
 
 // P - rho/3 in FP32, one reciprocal per EOS (Sec. 3.1 and Appendix G equations of state).
 // Every operation is an explicitly rounded intrinsic, so each inlined call
-// site rounds the same way (no call-site-dependent contraction).
-__device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
+// site rounds the same way (no call-site-dependent contraction). EOSK >= 0
+// fixes the equation of state at compile time (the same operations as its
+// case below); EOSK < 0 takes it from p.eos.
+template <int EOSK = -1>
+__device__ __forceinline__ float excess_pressure_ft(const PhysF &p, float rho)
 {
     const float br = __fmul_rn(p.b, rho), rr = __fmul_rn(rho, rho);
     const float nr3 = __fmul_rn(rho, -1.0f / 3.0f);
     const float rt = __fmul_rn(rho, p.RT);
-    switch (p.eos) {
+    switch (EOSK >= 0 ? EOSK : p.eos) {
     case 0:   // rho RT / (1 - b rho) - a rho^2 - rho/3
         return __fmaf_rn(-p.a, rr, __fmaf_rn(rt, __frcp_rn(__fsub_rn(1.0f, br)), nr3));
     case 1: {   // PR: d1 = 1 - b rho, d2 = 1 + 2 b rho - (b rho)^2
@@ -147,6 +150,11 @@ __device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
         return __fmaf_rn(-p.a, rr, __fmaf_rn(__fmul_rn(rt, poly), __frcp_rn(den), nr3));
     }
     }
+}
+
+__device__ __forceinline__ float excess_pressure_f(const PhysF &p, float rho)
+{
+    return excess_pressure_ft<-1>(p, rho);
 }
 
 // P - rho/3 in FP64: the same equations of state, for the FP64-EOS form of
@@ -513,7 +521,7 @@ __device__ __forceinline__ void load_from_box(const BoxS &b, int r, int c, V &v)
 }
 
 template <int LAT, bool MASK, bool TM = false, bool E64 = false, bool TMX = false, bool BOXED = false,
-          typename ST, typename SM>
+          int EOSK = -1, typename ST, typename SM>
 __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
                                         const uint8_t *__restrict__ mask,
                                         const ST *__restrict__ f, SM &sm, const TileF &T,
@@ -609,7 +617,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
                 d = (float)dd;
                 psi64 = (float)sqrt(fabs(dd));
             } else {
-                d = excess_pressure_f(p, rho);
+                d = excess_pressure_ft<EOSK>(p, rho);
             }
         }
         s_rp[rs][r][c] = f2(rho, E64 && !solid[u] ? psi64 : sqrtf(fabsf(d)));
@@ -949,8 +957,8 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 }
 
 // Wait (acquire) for the completion of the phase of the given parity;
-// false after kWaitCycles without it.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+// false after `limit` clock cycles without it.
+__device__ __forceinline__ bool mbar_wait_for(unsigned long long *bar, unsigned parity, long long limit)
 {
     const long long t0 = clock64();
     for (;;) {
@@ -961,8 +969,27 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
                      : "r"(smem_u32(bar)), "r"(parity)
                      : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    return mbar_wait_for(bar, parity, kWaitCycles);
+}
+
+// Self-test of the bounded waits: each warp of one block waits, through the
+// wait the fused kernels use, for a barrier phase that nothing completes
+// (no thread arrives), gives up after `limit` cycles, records it as the
+// kernels do (bit 2 of the status word) and returns. A template so that
+// only the build that launches it instantiates it.
+template <int N = 1>
+__global__ void k_wait_selftest(int *__restrict__ status, long long limit)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, N);
+    __syncthreads();
+    if (!mbar_wait_for(&bar, 0, limit) && (threadIdx.x & 31) == 0) atomicOr(status, 2);
 }
 
 // Shifted storage (ST 16-bit, SM = SharedSWS): the producers also keep the
@@ -1128,7 +1155,7 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
                  : "memory");
 }
 
-template <int LAT, bool MASK>
+template <int LAT, bool MASK, int EOSK>
 __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
                                                  const uint8_t *__restrict__ mask,
                                                  const float *__restrict__ f, float *__restrict__ fout,
@@ -1216,8 +1243,8 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
                 break;
             }
             tmem_fence_after();
-            phase_a<LAT, MASK, true, false, true, true>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase,
-                                                        &sm.box[pl % kBoxStages]);
+            phase_a<LAT, MASK, true, false, true, true, EOSK>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase,
+                                                              &sm.box[pl % kBoxStages]);
             tmem_fence_before();
             mbar_arrive(&sm.full[pl % 6]);
         }
@@ -1255,9 +1282,10 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
 // Warp-specialised with Tensor Memory staging and TMA staging of each
 // entering plane's halo (D3Q27 FP32 32 x 8 tiles; nx a multiple of 4, so
 // the tensor's rows are 16-byte aligned); maps are the source population
-// buffer f as a 4D tensor (x, y, z, i) with the four box shapes; dynamic
-// shared memory of sizeof(SharedWT<LAT>).
-template <int LAT, bool MASK>
+// buffer f as a 4D tensor (x, y, z, i) with the four box shapes; EOSK the
+// equation of state (p.eos) fixed at compile time; dynamic shared memory
+// of sizeof(SharedWT<LAT>).
+template <int LAT, bool MASK, int EOSK>
 __global__ void __launch_bounds__(2 * LatF<LAT>::TX * LatF<LAT>::TY, 1)
 k_step_f32_wstma(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const __grid_constant__ BoxMaps maps,
                  const float *__restrict__ f, float *__restrict__ fout, int *__restrict__ status)
@@ -1270,8 +1298,8 @@ k_step_f32_wstma(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const __grid
     __syncthreads();
     tmem_fence_after();
     const unsigned tbase = sm.tmem;
-    fused_tile_wstma<LAT, MASK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm, tbase,
-                                &maps);
+    fused_tile_wstma<LAT, MASK, EOSK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm,
+                                      tbase, &maps);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();

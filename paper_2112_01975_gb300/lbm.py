@@ -65,6 +65,7 @@ def _load():
     L.lbm_launch_count.restype = i64
     L.lbm_launch_count.argtypes = [vp]
     L.lbm_probe_fp64_tflops.argtypes = [dp]
+    L.lbm_selftest_wait_timeout.argtypes = [C.c_longlong, C.POINTER(C.c_int), dp]
     L.lbm_time_kernels.argtypes = [vp, i64, dp]
     L.lbm_set_chunk.argtypes = [vp, C.c_int]
     L.lbm_autotune.argtypes = [vp, C.POINTER(C.c_int)]
@@ -127,6 +128,16 @@ def probe_fp64_tflops() -> float:
     if rc:
         raise LBMError(rc, "FP64 probe failed")
     return v.value
+
+
+def selftest_wait_timeout(limit_cycles: int):
+    """Run the bounded-wait self-test: returns (status word, milliseconds);
+    the word is 2 when the waits ran out after limit_cycles and returned."""
+    st, ms = C.c_int(-1), C.c_double()
+    rc = _lib.lbm_selftest_wait_timeout(int(limit_cycles), C.byref(st), C.byref(ms))
+    if rc:
+        raise LBMError(rc, "wait self-test failed")
+    return st.value, ms.value
 
 
 def default_params(eos: int) -> lbm_params:

@@ -96,6 +96,9 @@ def test_null_handle_calls_are_errors(lib):
     assert lib.lbm_set_fused_variant(None, 1) == 1
     assert lib.lbm_get_fused_variant(None, C.byref(on)) == 1 and on.value == -1
     assert lib.lbm_probe_fp64_tflops(None) == 1
+    ms = C.c_double()
+    assert lib.lbm_selftest_wait_timeout(C.c_longlong(1000), None, C.byref(ms)) == 1
+    assert lib.lbm_selftest_wait_timeout(C.c_longlong(0), C.byref(on), C.byref(ms)) == 1
     lib.lbm_last_error.restype = C.c_char_p
     assert lib.lbm_last_error(None) == b"null handle"
     lib.lbm_destroy(None)

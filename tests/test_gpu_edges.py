@@ -90,3 +90,18 @@ def test_fp64_probe_measures_a_plausible_rate(lbm):
     b = lbm.probe_fp64_tflops()
     assert 0.125 < a < 3.75, a
     assert abs(a - b) < 0.1 * max(a, b), (a, b)
+
+
+def test_bounded_wait_runs_out_and_returns(lbm):
+    """The fused kernels' bounded wait, made to run out on a barrier phase
+    that nothing completes (2e6 cycles, about a millisecond): every waiting
+    warp records the timeout in the status word and the kernel returns; the
+    context stays usable (a step on a fresh lattice afterwards is fine)."""
+    st, ms = lbm.selftest_wait_timeout(2_000_000)
+    assert st == 2, st
+    assert 0.0 < ms < 200.0, ms
+    w = inputs.DROP_D3Q27_128
+    g = lbm.LBM(1, 24, 20, 16, w.eos, w.t_over_tc, w.kappa, 1.0, a=w.a, b=w.b, storage=1)
+    g.init(inputs.drop(24, 20, 16, 5.0, w.rho_v, w.rho_l))
+    g.step(4)
+    g.sync()
