@@ -273,7 +273,7 @@ int lbm_time_kernels(lbm_handle h, int64_t n, double *ms);
 int lbm_set_chunk(lbm_handle h, int chunk);
 
 /* Pick the chunk of the fused FP32 step by timing candidates (4 to 128
- * planes, and the whole march axis when it is longer) on the
+ * planes and, on a longer march axis, 10/16 to 16/16 of it) on the
  * handle's own state (saved to a temporary device buffer and restored
  * afterwards, so the state is unchanged). Sets and returns it in
  * *chunk_out (0 for FP64 storage, which has no tile parameter). With

@@ -58,8 +58,9 @@ struct lbm_ctx {
     int *poll_host = nullptr;
     cudaEvent_t poll_ev = nullptr;
     bool poll_pending = false;
-    // D3Q27 FP32 with nx % 4 == 0: the two population buffers as 4D tensors
-    // (x, y, z, i) for the TMA-staged form (LBM_FUSED_WS_TMA)
+    // D3Q27, FP32 with nx % 4 == 0 or shifted 16-bit with nx % 8 == 0: the
+    // two population buffers as 4D tensors (x, y, z, i) for the TMA-staged
+    // form (LBM_FUSED_WS_TMA)
     lbmf::BoxMaps tmaps[2];
     bool tmap_ready = false;
     // interpolated bounce-back: boundary nodes, their active links, wall distances
@@ -270,16 +271,22 @@ int ensure_memory(lbm_ctx *h)
 
 bool has_solid(const lbm_ctx *h) { return h->any_solid; }
 
-// The two population buffers of a D3Q27 FP32 handle as 4D tensors (x, y, z,
-// i) of FP32, each with the four box shapes of the TMA-staged form (32 x 8,
-// 32 x 2, 4 x 8 and 4 x 2 nodes of one plane, all 27 populations). Needs
-// nx % 4 == 0 (16-byte row strides) and the driver's tensor-map encoder,
-// found through the runtime's entry-point query; leaves tmap_ready false
-// when either is missing.
+// Row alignment the TMA-staged form needs: nx a multiple of 4 (FP32) or 8
+// (16-bit shifted storage), so that rows start on 16 bytes.
+int tma_nx_multiple(int storage) { return storage == LBM_F32 ? 4 : shifted(storage) ? 8 : 0; }
+
+// The two population buffers of a D3Q27 FP32 or shifted-storage handle as
+// 4D tensors (x, y, z, i) of the stored type, each with the four box shapes
+// of the TMA-staged form (32 x 8, 32 x 2, W x 8 and W x 2 nodes of one
+// plane, all 27 populations; W = 16 bytes of the type). Needs nx a multiple
+// of tma_nx_multiple (16-byte row strides) and the driver's tensor-map
+// encoder, found through the runtime's entry-point query; leaves tmap_ready
+// false when either is missing.
 void make_tensor_maps(lbm_ctx *h)
 {
     h->tmap_ready = false;
-    if (h->lattice != LBM_D3Q27 || h->storage != LBM_F32 || h->geo.nx % 4 || !h->fv[0]) return;
+    const int mult = tma_nx_multiple(h->storage);
+    if (h->lattice != LBM_D3Q27 || !mult || h->geo.nx % mult || !h->fv[0]) return;
     using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                 CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -293,17 +300,22 @@ void make_tensor_maps(lbm_ctx *h)
         return;
     }
     const Geo &g = h->geo;
+    const cuuint64_t es = pop_bytes(h->storage);
+    const CUtensorMapDataType dt = h->storage == LBM_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : h->storage == LBM_F16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint32_t w = (cuuint32_t)(16 / es);
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 27};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)g.N * 4};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nx * g.ny * es, (cuuint64_t)g.N * es};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int k = 0; k < 2; ++k) {
         CUtensorMap *m[4] = {&h->tmaps[k].mc, &h->tmaps[k].tc, &h->tmaps[k].ml, &h->tmaps[k].tl};
-        const cuuint32_t wx[4] = {32, 32, 4, 4}, wy[4] = {8, 2, 8, 2};
+        const cuuint32_t wx[4] = {32, 32, w, w}, wy[4] = {8, 2, 8, 2};
         for (int j = 0; j < 4; ++j) {
             const cuuint32_t box[4] = {wx[j], wy[j], 1, 27};
-            if (reinterpret_cast<Encode>(fn)(m[j], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->fv[k], dims, strides,
-                                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            if (reinterpret_cast<Encode>(fn)(m[j], dt, 4, h->fv[k], dims, strides, box, estr,
+                                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return;
         }
@@ -493,6 +505,11 @@ void launch_shifted_wstm(lbm_ctx *h, cudaStream_t s, int k)
 template <int LAT, typename ST, bool MASK>
 void launch_shifted_m(lbm_ctx *h, cudaStream_t s, int k)
 {
+    if (LAT == 1 && !h->e64 && h->variant == LBM_FUSED_WS_TMA) {   // tensor maps made
+        lbmtma::launch_shifted(h->geof, h->physf, h->mask, h->tmaps[k], static_cast<const ST *>(h->fv[k]),
+                               static_cast<ST *>(h->fv[k ^ 1]), h->rs[k], h->rs[k ^ 1], h->status, MASK, s);
+        return;
+    }
     if (h->e64) launch_shifted_e<LAT, ST, true, MASK>(h, s, k);
     else if (h->variant == LBM_FUSED_TMEM) launch_shifted_tm<LAT, ST, MASK>(h, s, k);
     else if (LAT == 1 && h->variant == LBM_FUSED_WS_TMEM) launch_shifted_wstm<ST, MASK>(h, s, k);
@@ -1640,8 +1657,12 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
         CU(h, cudaMemcpyAsync(static_cast<char *>(save) + bytes, h->rs[h->cur], rbytes,
                               cudaMemcpyDeviceToDevice, h->stream));
     const int nz = h->geof.nz;
-    // plane chunks per CTA; the last, the whole march axis (one chunk per column)
-    const int cands[] = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128, nz > 128 ? nz : 128};
+    // plane chunks per CTA; on a march axis longer than 128 planes also 10/16
+    // .. 16/16 of it: one long chunk per column and a short one after it,
+    // whose blocks (launched after all long ones) fill the last wave
+    std::vector<int> cands = {4, 6, 8, 11, 13, 16, 22, 26, 32, 43, 64, 128};
+    if (nz > 128)
+        for (int k = 10; k <= 16; ++k) cands.push_back(std::max(129, nz * k / 16));
     const int chunk0 = h->geof.chunk, rows0 = h->tile_rows;   // restored on failure
     // FP32: the plain, warp-specialised and Tensor Memory kernels; D3Q27 FP32
     // also 32 x 8 and 32 x 7 tiles (the shifted and batched steps use plain
@@ -1652,15 +1673,15 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     int best = h->geof.chunk, best_rows = h->tile_rows, best_variant = h->variant;
     double best_ms = 1e30;
     for (int var = 0; var <= LBM_FUSED_WS_TMA && rc == LBM_OK; ++var) {
-        // shifted storage: plain, Tensor Memory and (D3Q27) warp-specialised Tensor Memory
-        if (var > 0 && (h->e64 || (!fp32 && var != LBM_FUSED_TMEM && var != LBM_FUSED_WS_TMEM))) continue;
+        // shifted storage: plain, Tensor Memory and (D3Q27) the two warp-specialised Tensor Memory forms
+        if (var > 0 && (h->e64 || (!fp32 && var == LBM_FUSED_WARP_SPECIALISED))) continue;
         if (var >= LBM_FUSED_WS_TMEM && h->lattice != LBM_D3Q27) continue;
         if (var == LBM_FUSED_WS_TMA && !h->tmap_ready) continue;
         h->variant = var;
         for (int rows : {8, 7}) {
             if (rows == 7 && (!two_heights || var >= LBM_FUSED_WS_TMEM)) continue;
             h->tile_rows = rows;
-            for (int j = 0; j < (int)(sizeof cands / sizeof cands[0]); ++j) {
+            for (size_t j = 0; j < cands.size(); ++j) {
                 const int c = cands[j];
                 if ((c > nz && j != 0) || (j > 0 && c == cands[j - 1])) continue;
                 h->geof.chunk = c;
@@ -1734,15 +1755,16 @@ int lbm_set_fused_variant(lbm_handle h, int variant)
     if (variant >= LBM_FUSED_WS_TMEM && (h->lattice != LBM_D3Q27 || h->tile_rows != 8))
         return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory forms run D3Q27 32 x 8 tiles");
     if (variant == LBM_FUSED_WS_TMA &&
-        (h->storage != LBM_F32 || h->geo.nx % 4 || (h->fv[0] && !h->tmap_ready)))
-        return fail(h, LBM_EINVAL, "the TMA-staged form needs FP32 storage, nx a multiple of 4 and the "
-                                   "driver's tensor-map encoder");
+        (!tma_nx_multiple(h->storage) || h->geo.nx % tma_nx_multiple(h->storage) ||
+         (h->fv[0] && !h->tmap_ready)))
+        return fail(h, LBM_EINVAL, "the TMA-staged form needs FP32 storage with nx a multiple of 4 or shifted "
+                                   "storage with nx a multiple of 8, and the driver's tensor-map encoder");
     if (h->storage == LBM_F64 && variant != LBM_FUSED_PLAIN)
         return fail(h, LBM_EINVAL, "the FP64 step has one form");
     if (h->e64 && variant != LBM_FUSED_PLAIN)
         return fail(h, LBM_EINVAL, "the FP64-EOS step has one form");
-    if (shifted(h->storage) && (variant == LBM_FUSED_WARP_SPECIALISED || variant == LBM_FUSED_WS_TMA))
-        return fail(h, LBM_EINVAL, "shifted storage has the plain and the two Tensor Memory forms");
+    if (shifted(h->storage) && variant == LBM_FUSED_WARP_SPECIALISED)
+        return fail(h, LBM_EINVAL, "shifted storage has the plain and the Tensor Memory forms");
     if (h->variant != variant && h->graph) {   // the captured graph holds the other kernel
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;

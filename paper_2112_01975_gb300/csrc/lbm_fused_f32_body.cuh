@@ -438,32 +438,39 @@ __device__ __forceinline__ TileF tile_setup(const GeoF &g, int bx, int by, int b
 //
 // The box of one plane in nine dense TMA boxes (D3Q27 32 x 8 tiles): rows
 // top (y0 - 2, y0 - 1), middle (y0 .. y0 + 7), bottom (y0 + 8, y0 + 9) by
-// columns left (x0 - 4 .. x0 - 1), centre (x0 .. x0 + 31), right (x0 + 32 ..
-// x0 + 35), each [i][row][column] and fetched from its own wrapped origin,
-// so that a tile on the lattice's edge finds its periodic halo there too.
-// Left and right boxes are four columns wide, the narrowest a box with
-// 16-byte aligned rows can be (halo columns x0 - 2, x0 - 1 and x0 + 32,
-// x0 + 33 are its last two and first two). A tiled bulk tensor copy writes
-// shared memory from a 128-byte aligned address, so each box starts on one
-// (the 864-byte corners are padded to 896).
-struct BoxS {
-    static constexpr int Q = 27;
-    alignas(128) float mc[Q][8][32];
-    alignas(128) float tc[Q][2][32];
-    alignas(128) float bc[Q][2][32];
-    alignas(128) float ml[Q][8][4];
-    alignas(128) float mr[Q][8][4];
-    alignas(128) float tl[Q][2][4];
-    alignas(128) float tr[Q][2][4];
-    alignas(128) float bl[Q][2][4];
-    alignas(128) float br[Q][2][4];
+// columns left (x0 - W .. x0 - 1), centre (x0 .. x0 + 31), right (x0 + 32 ..
+// x0 + 31 + W), each [i][row][column] of the stored type ST and fetched from
+// its own wrapped origin, so that a tile on the lattice's edge finds its
+// periodic halo there too. Left and right boxes are W = 16 bytes wide (4
+// FP32 or 8 16-bit columns), the narrowest a box with 16-byte aligned rows
+// can be (halo columns x0 - 2, x0 - 1 and x0 + 32, x0 + 33 are its last two
+// and first two). A tiled bulk tensor copy writes shared memory from a
+// 128-byte aligned address, so each box starts on one (FP32 corners of 864
+// bytes are padded to 896).
+template <typename ST> struct BoxT {
+    static constexpr int Q = 27, W = 16 / (int)sizeof(ST);
+    alignas(128) ST mc[Q][8][32];
+    alignas(128) ST tc[Q][2][32];
+    alignas(128) ST bc[Q][2][32];
+    alignas(128) ST ml[Q][8][W];
+    alignas(128) ST mr[Q][8][W];
+    alignas(128) ST tl[Q][2][W];
+    alignas(128) ST tr[Q][2][W];
+    alignas(128) ST bl[Q][2][W];
+    alignas(128) ST br[Q][2][W];
     // bytes the nine copies of one plane deliver (without the padding)
-    static constexpr unsigned BYTES = Q * sizeof(float) * (8 * 32 + 2 * 2 * 32 + 2 * 8 * 4 + 4 * 2 * 4);
+    static constexpr unsigned BYTES = Q * sizeof(ST) * (8 * 32 + 2 * 2 * 32 + 2 * 8 * W + 4 * 2 * W);
 };
-static_assert(offsetof(BoxS, tc) % 128 == 0 && offsetof(BoxS, bc) % 128 == 0 && offsetof(BoxS, ml) % 128 == 0 &&
-                  offsetof(BoxS, mr) % 128 == 0 && offsetof(BoxS, tl) % 128 == 0 &&
-                  offsetof(BoxS, tr) % 128 == 0 && offsetof(BoxS, bl) % 128 == 0 &&
-                  offsetof(BoxS, br) % 128 == 0 && sizeof(BoxS) % 128 == 0,
+using BoxS = BoxT<float>;
+template <typename B>
+constexpr bool boxes_aligned()
+{
+    return offsetof(B, tc) % 128 == 0 && offsetof(B, bc) % 128 == 0 && offsetof(B, ml) % 128 == 0 &&
+           offsetof(B, mr) % 128 == 0 && offsetof(B, tl) % 128 == 0 && offsetof(B, tr) % 128 == 0 &&
+           offsetof(B, bl) % 128 == 0 && offsetof(B, br) % 128 == 0 && sizeof(B) % 128 == 0;
+}
+static_assert(boxes_aligned<BoxT<float>>() && boxes_aligned<BoxT<__half>>() &&
+                  boxes_aligned<BoxT<__nv_bfloat16>>(),
               "every box starts on a 128-byte boundary");
 
 // Halo node k of a 32 x 8 tile in the TMA-staged order: interior nodes first
@@ -493,30 +500,32 @@ __device__ __forceinline__ void halo_rc_boxed(int k, int &r, int &c)
     }
 }
 
-// Load the 27 populations of halo node (r, c) from the box into v.
-template <typename V>
-__device__ __forceinline__ void load_from_box(const BoxS &b, int r, int c, V &v)
+// The 27 populations of halo node (r, c) of ring plane pl from the box into
+// v, decoded (shifted storage) as decode_pop does.
+template <int LAT, bool MASK, typename ST, typename SM, typename V>
+__device__ __forceinline__ void load_from_box(const BoxT<ST> &b, int r, int c, int pl, const SM &sm, V &v)
 {
+    constexpr int W = BoxT<ST>::W;
     const int rc = r < 2 ? 0 : r < 10 ? 1 : 2;   // top, middle, bottom
     const int cc = c < 2 ? 0 : c < 34 ? 1 : 2;   // left, centre, right
     const int rr = rc == 0 ? r : rc == 1 ? r - 2 : r - 10;
-    const int xx = cc == 0 ? c + 2 : cc == 1 ? c - 2 : c - 34;
+    const int xx = cc == 0 ? c + W - 2 : cc == 1 ? c - 2 : c - 34;
     if (rc == 1 && cc == 1) {
 #pragma unroll
-        for (int i = 0; i < 27; ++i) v[i] = b.mc[i][rr][xx];
+        for (int i = 0; i < 27; ++i) v[i] = decode_pop<LAT, MASK>(b.mc[i][rr][xx], i, r, c, pl, sm);
     } else if (cc == 1) {
-        const float *q = rc == 0 ? &b.tc[0][rr][xx] : &b.bc[0][rr][xx];
+        const ST *q = rc == 0 ? &b.tc[0][rr][xx] : &b.bc[0][rr][xx];
 #pragma unroll
-        for (int i = 0; i < 27; ++i) v[i] = q[i * 64];
+        for (int i = 0; i < 27; ++i) v[i] = decode_pop<LAT, MASK>(q[i * 64], i, r, c, pl, sm);
     } else if (rc == 1) {
-        const float *q = cc == 0 ? &b.ml[0][rr][xx] : &b.mr[0][rr][xx];
+        const ST *q = cc == 0 ? &b.ml[0][rr][xx] : &b.mr[0][rr][xx];
 #pragma unroll
-        for (int i = 0; i < 27; ++i) v[i] = q[i * 32];
+        for (int i = 0; i < 27; ++i) v[i] = decode_pop<LAT, MASK>(q[i * 8 * W], i, r, c, pl, sm);
     } else {
-        const float *q = rc == 0 ? (cc == 0 ? &b.tl[0][rr][xx] : &b.tr[0][rr][xx])
-                                 : (cc == 0 ? &b.bl[0][rr][xx] : &b.br[0][rr][xx]);
+        const ST *q = rc == 0 ? (cc == 0 ? &b.tl[0][rr][xx] : &b.tr[0][rr][xx])
+                              : (cc == 0 ? &b.bl[0][rr][xx] : &b.br[0][rr][xx]);
 #pragma unroll
-        for (int i = 0; i < 27; ++i) v[i] = q[i * 8];
+        for (int i = 0; i < 27; ++i) v[i] = decode_pop<LAT, MASK>(q[i * 2 * W], i, r, c, pl, sm);
     }
 }
 
@@ -526,7 +535,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
                                         const uint8_t *__restrict__ mask,
                                         const ST *__restrict__ f, SM &sm, const TileF &T,
                                         int pl, int tid, const float *__restrict__ rho_src,
-                                        unsigned tbase = 0, const BoxS *box = nullptr)
+                                        unsigned tbase = 0, const BoxT<ST> *box = nullptr)
 {
     constexpr bool SHIFT = IsShifted<ST>::value;
     using L = LatF<LAT>;
@@ -569,7 +578,7 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
             bool in_box = false;
             if constexpr (BOXED) in_box = sm.xok[c] && sm.yok[r];
             if (in_box) {
-                if constexpr (BOXED) load_from_box(*box, r, c, fi[u]);
+                if constexpr (BOXED) load_from_box<LAT, MASK>(*box, r, c, pl, sm, fi[u]);
             } else {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT, MASK>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
@@ -1123,18 +1132,22 @@ constexpr int kBoxWarp = 7;
 constexpr int kBoxStages = 3, kBoxAhead = kBoxStages - 1;
 
 // The four box shapes as tensor maps of one population buffer: 32 x 8,
-// 32 x 2, 4 x 8 and 4 x 2 (x by y), one plane, all 27 populations.
+// 32 x 2, W x 8 and W x 2 (x by y), one plane, all 27 populations.
 struct BoxMaps {
     CUtensorMap mc, tc, ml, tl;
 };
 
-template <int LAT> struct SharedWT : SharedWS<LAT> {
-    alignas(128) BoxS box[kBoxStages];
+// Shared memory of the TMA-staged tile: that of the warp-specialised tile
+// (BASE: SharedWS, or SharedSWS for shifted storage) and the box stages.
+template <int LAT, typename ST, typename BASE> struct SharedWTT : BASE {
+    alignas(128) BoxT<ST> box[kBoxStages];
     unsigned long long bfull[kBoxStages];
     // the box holds halo column c / row r (its source coordinate is the
     // node's wrapped one; false only on ragged tiles)
     unsigned char xok[SharedF<LAT>::AX], yok[SharedF<LAT>::AY];
 };
+template <int LAT> using SharedWT = SharedWTT<LAT, float, SharedWS<LAT>>;
+template <int LAT, typename ST> using SharedSWT = SharedWTT<LAT, ST, SharedSWS<LAT>>;
 
 // Arm bar for `bytes` more bytes (one arrival).
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
@@ -1155,24 +1168,32 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
                  : "memory");
 }
 
-template <int LAT, bool MASK, int EOSK>
+// Shifted storage (ST 16-bit, SM = SharedSWT): the producers also keep the
+// source-density ring and wait for one another once per plane (pbar), as
+// in fused_tile_ws; the boxes hold the stored 16-bit values, which phase A
+// decodes.
+template <int LAT, bool MASK, int EOSK, typename ST = float, typename SM = SharedWT<LAT>>
 __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
                                                  const uint8_t *__restrict__ mask,
-                                                 const float *__restrict__ f, float *__restrict__ fout,
+                                                 const ST *__restrict__ f, ST *__restrict__ fout,
                                                  int *__restrict__ status, int bx, int by, int bz,
-                                                 SharedWT<LAT> &sm, unsigned tbase, const BoxMaps *maps)
+                                                 SM &sm, unsigned tbase, const BoxMaps *maps,
+                                                 const float *__restrict__ rho_src = nullptr,
+                                                 float *__restrict__ rho_dst = nullptr)
 {
+    constexpr bool SHIFT = IsShifted<ST>::value;
     constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
     constexpr int AX = SharedF<LAT>::AX, AY = SharedF<LAT>::AY;
+    constexpr int W = BoxT<ST>::W;
     static_assert(LAT == 1 && TX == 32 && LatF<LAT>::TY == 8, "the box layout is that of D3Q27 32 x 8 tiles");
     const int tid = threadIdx.x;
-    const TileF T = tile_setup<LAT, float>(g, bx, by, bz, sm, tid, 2 * NT, nullptr);
-    // box origins: columns x0 - 4, x0, x0 + 32 and rows y0 - 2, y0, y0 + 8, wrapped
-    const int xl = ((T.x0 - 4) % g.nx + g.nx) % g.nx, xr = (T.x0 + 32) % g.nx;
+    const TileF T = tile_setup<LAT, ST>(g, bx, by, bz, sm, tid, 2 * NT, rho_src);
+    // box origins: columns x0 - W, x0, x0 + 32 and rows y0 - 2, y0, y0 + 8, wrapped
+    const int xl = ((T.x0 - W) % g.nx + g.nx) % g.nx, xr = (T.x0 + 32) % g.nx;
     const int yt = ((T.y0 - 2) % g.ny + g.ny) % g.ny, yb = (T.y0 + 8) % g.ny;
     if (tid < AX) {   // (the wrapped coordinates formed here, not read from tile_setup's)
         const int c = tid;
-        const int xs = c < 2 ? xl + c + 2 : c < 34 ? T.x0 + c - 2 : xr + c - 34;
+        const int xs = c < 2 ? xl + c + W - 2 : c < 34 ? T.x0 + c - 2 : xr + c - 34;
         sm.xok[c] = xs < g.nx && xs == ((T.x0 - 2 + c) % g.nx + g.nx) % g.nx;
     } else if (tid < AX + AY) {
         const int r = tid - AX;
@@ -1185,6 +1206,8 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
             mbar_init(&sm.empty[k], NT);
         }
         for (int k = 0; k < kBoxStages; ++k) mbar_init(&sm.bfull[k], 1);
+        if constexpr (SHIFT)
+            for (int k = 0; k < 2; ++k) mbar_init(&sm.pbar[k], NT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -1198,10 +1221,10 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
     // the nine boxes of ring index r (plane z0 - 2 + r) into stage r % kBoxStages
     auto request = [&](int r) {
         const int st = r % kBoxStages;
-        BoxS &b = sm.box[st];
+        BoxT<ST> &b = sm.box[st];
         unsigned long long *bar = &sm.bfull[st];
         const int z = wrapf(T.z0 - 2 + r, g.nz);
-        mbar_expect_tx(bar, BoxS::BYTES);
+        mbar_expect_tx(bar, BoxT<ST>::BYTES);
         tma_load_4d(&b.mc[0][0][0], &maps->mc, bar, T.x0, T.y0, z);
         tma_load_4d(&b.tc[0][0][0], &maps->tc, bar, T.x0, yt, z);
         tma_load_4d(&b.bc[0][0][0], &maps->tc, bar, T.x0, yb, z);
@@ -1242,10 +1265,17 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
                 atomicOr(status, 2);
                 break;
             }
+            if constexpr (SHIFT) {   // the source densities loaded in iteration pl - 1 are in place
+                if (pl > 0 && !mbar_wait(&sm.pbar[(pl - 1) & 1], ((pl - 1) >> 1) & 1)) {
+                    atomicOr(status, 2);
+                    break;
+                }
+            }
             tmem_fence_after();
-            phase_a<LAT, MASK, true, false, true, true, EOSK>(g, p, mask, f, sm, T, pl, tid, nullptr, tbase,
+            phase_a<LAT, MASK, true, false, true, true, EOSK>(g, p, mask, f, sm, T, pl, tid, rho_src, tbase,
                                                               &sm.box[pl % kBoxStages]);
             tmem_fence_before();
+            if constexpr (SHIFT) mbar_arrive(&sm.pbar[pl & 1]);
             mbar_arrive(&sm.full[pl % 6]);
         }
         // After a wait ran out, the boxes requested but not yet seen to land
@@ -1267,10 +1297,10 @@ __device__ __forceinline__ void fused_tile_wstma(const GeoF &g, const PhysF &p,
                 // the solid-node code only where a node or one of its
                 // neighbours can be solid (planes zc - 1 .. zc + 1)
                 if (MASK && planes_solid3(g, T.z0 + pl - 4))
-                    phase_b<LAT, true, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr,
+                    phase_b<LAT, true, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, rho_dst,
                                                           tbase, inside);
                 else
-                    phase_b<LAT, false, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, nullptr,
+                    phase_b<LAT, false, true, false, true>(g, p, mask, f, fout, status, sm, T, pl, t, rho_dst,
                                                            tbase, inside);
                 tmem_fence_before();
                 mbar_arrive(&sm.empty[pl % 6]);
@@ -1300,6 +1330,32 @@ k_step_f32_wstma(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const __grid
     const unsigned tbase = sm.tmem;
     fused_tile_wstma<LAT, MASK, EOSK>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm,
                                       tbase, &maps);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, COLS);
+}
+
+// Shifted 16-bit storage, TMA-staged (D3Q27 32 x 8 tiles; nx a multiple of 8,
+// so the 16-bit tensor's rows are 16-byte aligned): the boxes carry the
+// stored values, the source densities come through the producers' ring;
+// dynamic shared memory of sizeof(SharedSWT<LAT, ST>).
+template <int LAT, typename ST, bool MASK>
+__global__ void __launch_bounds__(2 * LatF<LAT>::TX * LatF<LAT>::TY, 1)
+k_step_shifted_wstma(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const __grid_constant__ BoxMaps maps,
+                     const ST *__restrict__ f, ST *__restrict__ fout, const float *__restrict__ rho_src,
+                     float *__restrict__ rho_dst, int *__restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw128[];
+    SharedSWT<LAT, ST> &sm = *reinterpret_cast<SharedSWT<LAT, ST> *>(smem_raw128);
+    constexpr unsigned COLS = TmemF<LAT>::COLS;
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned tbase = sm.tmem;
+    fused_tile_wstma<LAT, MASK, -1, ST, SharedSWT<LAT, ST>>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y,
+                                                            blockIdx.z, sm, tbase, &maps, rho_src, rho_dst);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();

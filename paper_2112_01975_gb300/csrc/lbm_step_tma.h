@@ -18,4 +18,12 @@ namespace lbmtma {
 void launch(const lbmf::GeoF &g, const lbmf::PhysF &p, const uint8_t *mask, const lbmf::BoxMaps &maps,
             const float *src, float *dst, int *status, bool solid, cudaStream_t s);
 
+// The same for shifted 16-bit storage (ST __half or __nv_bfloat16): src/dst
+// the stored values, rho_src/rho_dst their source densities; the equation
+// of state is taken from p.eos at run time.
+template <typename ST>
+void launch_shifted(const lbmf::GeoF &g, const lbmf::PhysF &p, const uint8_t *mask, const lbmf::BoxMaps &maps,
+                    const ST *src, ST *dst, const float *rho_src, float *rho_dst, int *status, bool solid,
+                    cudaStream_t s);
+
 }  // namespace lbmtma

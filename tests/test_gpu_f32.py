@@ -222,10 +222,11 @@ def test_f32_tma_staged_form_is_bitwise_the_plain_form(lbm, shape, chunk, solid)
 
 
 def test_f32_tma_staged_form_rejects_other_cases(lbm):
-    """nx not a multiple of 4 (rows not 16-byte aligned), D2Q9, 7-row tiles
-    and shifted storage have no TMA-staged form."""
+    """Rows not 16-byte aligned (nx not a multiple of 4 for FP32, of 8 for
+    16-bit shifted storage), D2Q9, FP64 storage and 7-row tiles have no
+    TMA-staged form."""
     w = inputs.DROP_D3Q27_128
-    for nx, lattice, storage in ((37, 1, lbm.F32), (64, 0, lbm.F32), (64, 1, lbm.F16S)):
+    for nx, lattice, storage in ((37, 1, lbm.F32), (64, 0, lbm.F32), (60, 1, lbm.F16S), (64, 1, lbm.F64)):
         g = lbm.LBM(lattice, nx, 16 if lattice else 64, 12 if lattice else 1, w.eos, w.t_over_tc,
                     w.kappa, w.tau, a=w.a, b=w.b, storage=storage)
         with pytest.raises(lbm.LBMError):
