@@ -300,9 +300,8 @@ int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y);
 int lbm_set_tile(lbm_handle h, int tile_y);
 
 /* Forms of the fused step of the reduced storages (LBM_F32; LBM_F16S and
- * LBM_BF16S have the plain, the Tensor Memory and, for D3Q27, the
- * warp-specialised Tensor Memory form); the same arithmetic in the same
- * order, so results are bitwise the same whichever runs.
+ * LBM_BF16S have all but LBM_FUSED_WARP_SPECIALISED); the same arithmetic in
+ * the same order, so results are bitwise the same whichever runs.
  *   LBM_FUSED_PLAIN (default): one thread group per tile; each entering
  *     plane's densities, pseudo-potentials and velocities are formed, the
  *     block synchronises, and the plane two behind collides and streams,
@@ -329,21 +328,22 @@ enum {
  *     warp-specialised form with the Tensor Memory staging, the producer that
  *     loads a node leaving its populations in the lane of the consumer that
  *     collides it.
- *   LBM_FUSED_WS_TMA (D3Q27 FP32, 32 x 8 tiles, nx a multiple of 4): the
- *     LBM_FUSED_WS_TMEM form with each entering plane's populations on the
- *     tile's halo copied into shared memory by the tensor-memory-access unit
- *     (one bulk tensor copy per plane, requested two planes ahead) instead
- *     of loaded by the producers; 215 KB of shared memory per block. The
+ *   LBM_FUSED_WS_TMA (D3Q27, 32 x 8 tiles; FP32 with nx a multiple of 4, or
+ *     shifted storage with nx a multiple of 8): the LBM_FUSED_WS_TMEM form
+ *     with each entering plane's populations on the tile's halo copied into
+ *     shared memory by the tensor-memory-access unit (nine bulk tensor
+ *     copies per plane, requested two planes ahead) instead of loaded by the
+ *     producers; 215 KB (FP32) or 175 KB of shared memory per block. The
  *     tensor maps are made when the handle's device memory is laid out; if
  *     the driver offers no tensor-map encoder there, a handle set to this
  *     form runs LBM_FUSED_WS_TMEM (lbm_get_fused_variant says which).
  * Select a form of the fused step (lbm_autotune times the forms the
  * storage has). LBM_EINVAL for an unknown form, a form other than
  * LBM_FUSED_PLAIN with LBM_F64 storage or LBM_FLAG_EOS_F64, or
- * LBM_FUSED_WARP_SPECIALISED or LBM_FUSED_WS_TMA with shifted storage, or
- * LBM_FUSED_WS_TMEM or
- * LBM_FUSED_WS_TMA with D2Q9 or 7-row tiles, or LBM_FUSED_WS_TMA with nx not a
- * multiple of 4 or, after the memory is laid out, without tensor maps. */
+ * LBM_FUSED_WARP_SPECIALISED with shifted storage, or LBM_FUSED_WS_TMEM or
+ * LBM_FUSED_WS_TMA with D2Q9 or 7-row tiles, or LBM_FUSED_WS_TMA with nx not
+ * a multiple of 4 (FP32) or 8 (shifted) or, after the memory is laid out,
+ * without tensor maps. */
 int lbm_set_fused_variant(lbm_handle h, int variant);
 
 /* *variant = the form of the fused step in use. */
