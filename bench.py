@@ -70,11 +70,12 @@ def fp64_peak():
 # tile rows, fused-step form); each entry records the SHA-256 prefix of the fused kernel's
 # source it was taken on, and is not used once that source has changed.
 MEASURED_TRAFFIC = {
-    # k_step_f32_wstma, 32 x 8 tiles, chunk 256, on the impact scaled to
-    # 192x192x256: 1069.2 + 960.6 MB for 9,437,184 nodes
+    # k_step_f32_wstma, 32 x 8 tiles, chunk 208 (one 208-plane and one
+    # 48-plane chunk per column, as at full size), on the impact scaled to
+    # 192x192x256: 1113.9 + 968.1 MB for 9,437,184 nodes
     # (profiles/k_step_f32_wstma_d3q27_impact_192x192x256.md)
     ("d3q27_impact_384x384x256_pr_tr0.5", "f32", 8, 4): {
-        "bytes_per_node": 215.08, "src_sha": "33968f18fcdd6809"},
+        "bytes_per_node": 220.61, "src_sha": "91af72b360c2adf8"},
 }
 FUSED_SRC = os.path.join(ROOT, "paper_2112_01975_gb300", "csrc", "lbm_fused_f32_body.cuh")
 
