@@ -335,7 +335,7 @@ enum {
  *     copies per plane, requested two planes ahead) instead of loaded by the
  *     producers; 215 KB (FP32) or 175 KB of shared memory per block. The
  *     tensor maps are made when the handle's device memory is laid out; if
- *     the driver offers no tensor-map encoder there, a handle set to this
+ *     the CUDA driver offers no tensor-map encoder, a handle set to this
  *     form runs LBM_FUSED_WS_TMEM (lbm_get_fused_variant says which).
  * Select a form of the fused step (lbm_autotune times the forms the
  * storage has). LBM_EINVAL for an unknown form, a form other than

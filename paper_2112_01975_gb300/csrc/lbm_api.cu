@@ -279,7 +279,7 @@ int tma_nx_multiple(int storage) { return storage == LBM_F32 ? 4 : shifted(stora
 // 4D tensors (x, y, z, i) of the stored type, each with the four box shapes
 // of the TMA-staged form (32 x 8, 32 x 2, W x 8 and W x 2 nodes of one
 // plane, all 27 populations; W = 16 bytes of the type). Needs nx a multiple
-// of tma_nx_multiple (16-byte row strides) and the driver's tensor-map
+// of tma_nx_multiple (16-byte row strides) and the CUDA driver's tensor-map
 // encoder, found through the runtime's entry-point query; leaves tmap_ready
 // false when either is missing.
 void make_tensor_maps(lbm_ctx *h)
@@ -1758,7 +1758,7 @@ int lbm_set_fused_variant(lbm_handle h, int variant)
         (!tma_nx_multiple(h->storage) || h->geo.nx % tma_nx_multiple(h->storage) ||
          (h->fv[0] && !h->tmap_ready)))
         return fail(h, LBM_EINVAL, "the TMA-staged form needs FP32 storage with nx a multiple of 4 or shifted "
-                                   "storage with nx a multiple of 8, and the driver's tensor-map encoder");
+                                   "storage with nx a multiple of 8, and the CUDA driver's tensor-map encoder");
     if (h->storage == LBM_F64 && variant != LBM_FUSED_PLAIN)
         return fail(h, LBM_EINVAL, "the FP64 step has one form");
     if (h->e64 && variant != LBM_FUSED_PLAIN)
