@@ -275,6 +275,26 @@ def test_long_step_call_stops_at_a_nonfinite_density(lbm, storage):
     assert g.launches - l0 >= per_step * 4000
 
 
+def test_long_step_call_stops_in_the_tma_staged_form(lbm):
+    """The same status polling with the TMA-staged FP32 step (D3Q27, the
+    warp-specialised kernel whose waits are bounded): a NaN stops a
+    4000-step call with LBM_ENONFINITE within two polling intervals."""
+    g = lbm.LBM(1, 64, 16, 12, 0, 0.8, 0.02, 1.0, a=9 / 490, storage=lbm.F32)
+    g.set_fused_variant(lbm.FUSED_WS_TMA)
+    r = np.full(64 * 16 * 12, 2.0)
+    r[5000] = np.nan
+    g.init(r)
+    assert g.fused_variant == lbm.FUSED_WS_TMA
+    l0 = g.launches
+    with pytest.raises(lbm.LBMError) as e:
+        g.step(4000)
+    assert e.value.code == 4
+    assert g.launches - l0 <= 3 * 64 + 2
+    g.init(np.full(64 * 16 * 12, 2.0))
+    g.step(500)
+    g.sync(5000)
+
+
 def test_phi_off_flag_matches_oracle(lbm):
     from oracle.lbm import PHI_OFF
     nx = 64
