@@ -76,6 +76,11 @@ MEASURED_TRAFFIC = {
     # (profiles/k_step_f32_wstma_d3q27_impact_192x192x256.md)
     ("d3q27_impact_384x384x256_pr_tr0.5", "f32", 8, 4): {
         "bytes_per_node": 220.61, "src_sha": "91af72b360c2adf8"},
+    # k_step_shifted (FP16-shifted, plain form), 32 x 8 tiles, chunk 240, on
+    # the same scaled impact: 594.3 + 514.5 MB for 9,437,184 nodes
+    # (profiles/k_step_shifted_d3q27_impact_192x192x256.md)
+    ("d3q27_impact_384x384x256_pr_tr0.5", "f16s", 8, 0): {
+        "bytes_per_node": 117.50, "src_sha": "91af72b360c2adf8"},
 }
 FUSED_SRC = os.path.join(ROOT, "paper_2112_01975_gb300", "csrc", "lbm_fused_f32_body.cuh")
 
