@@ -72,15 +72,16 @@ def fp64_peak():
 MEASURED_TRAFFIC = {
     # k_step_f32_wstma, 32 x 8 tiles, chunk 208 (one 208-plane and one
     # 48-plane chunk per column, as at full size), on the impact scaled to
-    # 192x192x256: 1113.9 + 968.1 MB for 9,437,184 nodes
+    # 192x192x256: 1113.8 + 968.3 MB for 9,437,184 nodes
     # (profiles/k_step_f32_wstma_d3q27_impact_192x192x256.md)
     ("d3q27_impact_384x384x256_pr_tr0.5", "f32", 8, 4): {
-        "bytes_per_node": 220.61, "src_sha": "91af72b360c2adf8"},
-    # k_step_shifted (FP16-shifted, plain form), 32 x 8 tiles, chunk 240, on
-    # the same scaled impact: 594.3 + 514.5 MB for 9,437,184 nodes
-    # (profiles/k_step_shifted_d3q27_impact_192x192x256.md)
-    ("d3q27_impact_384x384x256_pr_tr0.5", "f16s", 8, 0): {
-        "bytes_per_node": 117.50, "src_sha": "91af72b360c2adf8"},
+        "bytes_per_node": 220.62, "src_sha": "7afd52481196669b"},
+    # k_step_shifted_tmtma (FP16-shifted, Tensor Memory with TMA-staged
+    # planes), 32 x 8 tiles, chunk 224, on the same scaled impact: 585.6 +
+    # 502.3 MB for 9,437,184 nodes
+    # (profiles/k_step_shifted_tmtma_d3q27_impact_192x192x256.md)
+    ("d3q27_impact_384x384x256_pr_tr0.5", "f16s", 8, 5): {
+        "bytes_per_node": 115.28, "src_sha": "7afd52481196669b"},
 }
 FUSED_SRC = os.path.join(ROOT, "paper_2112_01975_gb300", "csrc", "lbm_fused_f32_body.cuh")
 
@@ -112,9 +113,10 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the FP32 step")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 7, 8],
                     help="D3Q27 FP32 tile height (0: picked by the autotuner, or 8 with --chunk)")
-    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
                     help="fused-step form: 0 plain, 1 warp-specialised, 2 Tensor Memory, 3 "
-                         "warp-specialised with Tensor Memory, 4 the same with TMA-staged planes "
+                         "warp-specialised with Tensor Memory, 4 the same with TMA-staged planes, "
+                         "5 Tensor Memory with TMA-staged planes (shifted storage) "
                          "(-1: picked by the autotuner, or plain with --chunk)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64 side measurement")
@@ -575,7 +577,7 @@ def main():
         g.set_chunk(chunk)
         if args.tile and storage == F32 and w.lattice == 1:
             g.set_tile(args.tile)
-        if args.variant >= 0 and storage == F32:
+        if args.variant >= 0:
             g.set_fused_variant(args.variant)
     g.step(args.warmup)
     g.sync()
@@ -610,7 +612,9 @@ def main():
                                4: "k_step_f32_wstma (fused step, warp-specialised, Tensor Memory "
                                   "staging, TMA-staged planes)"}[variant]
                     if storage == F32 else
-                    ("k_step_shifted_tm" if variant == 2 else "k_step_shifted"),
+                    {0: "k_step_shifted", 2: "k_step_shifted_tm", 3: "k_step_shifted_wstm",
+                     4: "k_step_shifted_wstma", 5: "k_step_shifted_tmtma (Tensor Memory, TMA-staged planes)"}
+                    .get(variant, "k_step_shifted"),
                     "peak_source": peak_kind + " hbm_gbs (burst copy)",
                     "alg_bytes_per_launch": alg, "ms_per_launch": ms_launch,
                     "ms_per_launch_source": "CUDA events over the timed graph replays / launches",

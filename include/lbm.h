@@ -299,9 +299,10 @@ int lbm_get_tile(lbm_handle h, int *tile_x, int *tile_y);
  * storage. */
 int lbm_set_tile(lbm_handle h, int tile_y);
 
-/* Forms of the fused step of the reduced storages (LBM_F32; LBM_F16S and
- * LBM_BF16S have all but LBM_FUSED_WARP_SPECIALISED); the same arithmetic in
- * the same order, so results are bitwise the same whichever runs.
+/* Forms of the fused step of the reduced storages (LBM_F32 all but
+ * LBM_FUSED_TM_TMA; LBM_F16S and LBM_BF16S all but
+ * LBM_FUSED_WARP_SPECIALISED); the same arithmetic in the same order, so
+ * results are bitwise the same whichever runs.
  *   LBM_FUSED_PLAIN (default): one thread group per tile; each entering
  *     plane's densities, pseudo-potentials and velocities are formed, the
  *     block synchronises, and the plane two behind collides and streams,
@@ -321,7 +322,8 @@ enum {
     LBM_FUSED_WARP_SPECIALISED = 1,
     LBM_FUSED_TMEM = 2,
     LBM_FUSED_WS_TMEM = 3,
-    LBM_FUSED_WS_TMA = 4
+    LBM_FUSED_WS_TMA = 4,
+    LBM_FUSED_TM_TMA = 5
 };
 
 /*   LBM_FUSED_WS_TMEM (D3Q27, 32 x 8 tiles; FP32 or shifted storage): the
@@ -337,13 +339,20 @@ enum {
  *     tensor maps are made when the handle's device memory is laid out; if
  *     the CUDA driver offers no tensor-map encoder, a handle set to this
  *     form runs LBM_FUSED_WS_TMEM (lbm_get_fused_variant says which).
+ *   LBM_FUSED_TM_TMA (shifted storage only; D3Q27, 32 x 8 tiles, nx a
+ *     multiple of 8): the LBM_FUSED_TMEM form (one thread group, two blocks
+ *     per SM) with each entering plane copied into shared memory by the
+ *     tensor-memory-access unit in one stage, requested a phase ahead (one
+ *     copy per plane where the tile's halo stays inside the lattice, nine
+ *     elsewhere); without a tensor-map encoder it runs LBM_FUSED_TMEM.
  * Select a form of the fused step (lbm_autotune times the forms the
  * storage has). LBM_EINVAL for an unknown form, a form other than
  * LBM_FUSED_PLAIN with LBM_F64 storage or LBM_FLAG_EOS_F64, or
- * LBM_FUSED_WARP_SPECIALISED with shifted storage, or LBM_FUSED_WS_TMEM or
- * LBM_FUSED_WS_TMA with D2Q9 or 7-row tiles, or LBM_FUSED_WS_TMA with nx not
- * a multiple of 4 (FP32) or 8 (shifted) or, after the memory is laid out,
- * without tensor maps. */
+ * LBM_FUSED_WARP_SPECIALISED with shifted storage, LBM_FUSED_TM_TMA with
+ * LBM_F32, or LBM_FUSED_WS_TMEM, LBM_FUSED_WS_TMA or LBM_FUSED_TM_TMA with
+ * D2Q9 or 7-row tiles, or the TMA-staged forms with nx not a multiple of 4
+ * (FP32) or 8 (shifted) or, after the memory is laid out, without tensor
+ * maps. */
 int lbm_set_fused_variant(lbm_handle h, int variant);
 
 /* *variant = the form of the fused step in use. */

@@ -266,6 +266,7 @@ int ensure_memory(lbm_ctx *h)
     CU(h, cudaStreamSynchronize(h->stream));
     make_tensor_maps(h);
     if (h->variant == LBM_FUSED_WS_TMA && !h->tmap_ready) h->variant = LBM_FUSED_WS_TMEM;
+    if (h->variant == LBM_FUSED_TM_TMA && !h->tmap_ready) h->variant = LBM_FUSED_TMEM;
     return LBM_OK;
 }
 
@@ -276,9 +277,10 @@ bool has_solid(const lbm_ctx *h) { return h->any_solid; }
 int tma_nx_multiple(int storage) { return storage == LBM_F32 ? 4 : shifted(storage) ? 8 : 0; }
 
 // The two population buffers of a D3Q27 FP32 or shifted-storage handle as
-// 4D tensors (x, y, z, i) of the stored type, each with the four box shapes
-// of the TMA-staged form (32 x 8, 32 x 2, W x 8 and W x 2 nodes of one
-// plane, all 27 populations; W = 16 bytes of the type). Needs nx a multiple
+// 4D tensors (x, y, z, i) of the stored type, each with the five box shapes
+// of the TMA-staged forms (32 x 8, 32 x 2, W x 8, W x 2 and the one-copy
+// (32 + 2 W) x 12 nodes of one plane, all 27 populations; W = 16 bytes of
+// the type). Needs nx a multiple
 // of tma_nx_multiple (16-byte row strides) and the CUDA driver's tensor-map
 // encoder, found through the runtime's entry-point query; leaves tmap_ready
 // false when either is missing.
@@ -309,9 +311,10 @@ void make_tensor_maps(lbm_ctx *h)
     const cuuint64_t strides[3] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nx * g.ny * es, (cuuint64_t)g.N * es};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int k = 0; k < 2; ++k) {
-        CUtensorMap *m[4] = {&h->tmaps[k].mc, &h->tmaps[k].tc, &h->tmaps[k].ml, &h->tmaps[k].tl};
-        const cuuint32_t wx[4] = {32, 32, w, w}, wy[4] = {8, 2, 8, 2};
-        for (int j = 0; j < 4; ++j) {
+        CUtensorMap *m[5] = {&h->tmaps[k].mc, &h->tmaps[k].tc, &h->tmaps[k].ml, &h->tmaps[k].tl,
+                             &h->tmaps[k].wide};
+        const cuuint32_t wx[5] = {32, 32, w, w, 32 + 2 * w}, wy[5] = {8, 2, 8, 2, 12};
+        for (int j = 0; j < 5; ++j) {
             const cuuint32_t box[4] = {wx[j], wy[j], 1, 27};
             if (reinterpret_cast<Encode>(fn)(m[j], dt, 4, h->fv[k], dims, strides, box, estr,
                                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -508,6 +511,12 @@ void launch_shifted_m(lbm_ctx *h, cudaStream_t s, int k)
     if (LAT == 1 && !h->e64 && h->variant == LBM_FUSED_WS_TMA) {   // tensor maps made
         lbmtma::launch_shifted(h->geof, h->physf, h->mask, h->tmaps[k], static_cast<const ST *>(h->fv[k]),
                                static_cast<ST *>(h->fv[k ^ 1]), h->rs[k], h->rs[k ^ 1], h->status, MASK, s);
+        return;
+    }
+    if (LAT == 1 && !h->e64 && h->variant == LBM_FUSED_TM_TMA) {   // tensor maps made
+        lbmtma::launch_shifted_tm(h->geof, h->physf, h->mask, h->tmaps[k], static_cast<const ST *>(h->fv[k]),
+                                  static_cast<ST *>(h->fv[k ^ 1]), h->rs[k], h->rs[k ^ 1], h->status, MASK,
+                                  s);
         return;
     }
     if (h->e64) launch_shifted_e<LAT, ST, true, MASK>(h, s, k);
@@ -1672,11 +1681,12 @@ int lbm_autotune(lbm_handle h, int *chunk_out)
     const int variant0 = h->variant;
     int best = h->geof.chunk, best_rows = h->tile_rows, best_variant = h->variant;
     double best_ms = 1e30;
-    for (int var = 0; var <= LBM_FUSED_WS_TMA && rc == LBM_OK; ++var) {
+    for (int var = 0; var <= LBM_FUSED_TM_TMA && rc == LBM_OK; ++var) {
         // shifted storage: plain, Tensor Memory and (D3Q27) the two warp-specialised Tensor Memory forms
         if (var > 0 && (h->e64 || (!fp32 && var == LBM_FUSED_WARP_SPECIALISED))) continue;
         if (var >= LBM_FUSED_WS_TMEM && h->lattice != LBM_D3Q27) continue;
-        if (var == LBM_FUSED_WS_TMA && !h->tmap_ready) continue;
+        if ((var == LBM_FUSED_WS_TMA || var == LBM_FUSED_TM_TMA) && !h->tmap_ready) continue;
+        if (var == LBM_FUSED_TM_TMA && !shifted(h->storage)) continue;   // a form of shifted storage
         h->variant = var;
         for (int rows : {8, 7}) {
             if (rows == 7 && (!two_heights || var >= LBM_FUSED_WS_TMEM)) continue;
@@ -1750,11 +1760,13 @@ int lbm_set_tile(lbm_handle h, int tile_y)
 int lbm_set_fused_variant(lbm_handle h, int variant)
 {
     if (!h) return LBM_EINVAL;
-    if (variant < LBM_FUSED_PLAIN || variant > LBM_FUSED_WS_TMA)
+    if (variant < LBM_FUSED_PLAIN || variant > LBM_FUSED_TM_TMA)
         return fail(h, LBM_EINVAL, "unknown fused-step variant %d", variant);
+    if (variant == LBM_FUSED_TM_TMA && !shifted(h->storage))
+        return fail(h, LBM_EINVAL, "the one-group TMA-staged form is a form of shifted storage");
     if (variant >= LBM_FUSED_WS_TMEM && (h->lattice != LBM_D3Q27 || h->tile_rows != 8))
         return fail(h, LBM_EINVAL, "the warp-specialised Tensor Memory forms run D3Q27 32 x 8 tiles");
-    if (variant == LBM_FUSED_WS_TMA &&
+    if ((variant == LBM_FUSED_WS_TMA || variant == LBM_FUSED_TM_TMA) &&
         (!tma_nx_multiple(h->storage) || h->geo.nx % tma_nx_multiple(h->storage) ||
          (h->fv[0] && !h->tmap_ready)))
         return fail(h, LBM_EINVAL, "the TMA-staged form needs FP32 storage with nx a multiple of 4 or shifted "

@@ -460,8 +460,16 @@ template <typename ST> struct BoxT {
     alignas(128) ST br[Q][2][W];
     // bytes the nine copies of one plane deliver (without the padding)
     static constexpr unsigned BYTES = Q * sizeof(ST) * (8 * 32 + 2 * 2 * 32 + 2 * 8 * W + 4 * 2 * W);
+    // A tile whose halo neither wraps nor leaves the lattice can take the
+    // plane in one copy instead: [i][row][column], 12 rows of WX = 32 + 2 W
+    // columns from (x0 - W, y0 - 2), in the same space.
+    static constexpr int WX = 32 + 2 * W;
+    static constexpr unsigned WIDE_BYTES = Q * 12 * WX * sizeof(ST);
+    __device__ const ST *wide() const { return &mc[0][0][0]; }
 };
 using BoxS = BoxT<float>;
+static_assert(BoxT<float>::WIDE_BYTES <= sizeof(BoxT<float>) && BoxT<__half>::WIDE_BYTES <= sizeof(BoxT<__half>),
+              "the one-copy layout fits the nine boxes' space");
 template <typename B>
 constexpr bool boxes_aligned()
 {
@@ -500,6 +508,17 @@ __device__ __forceinline__ void halo_rc_boxed(int k, int &r, int &c)
     }
 }
 
+// The 27 populations of halo node (r, c) of ring plane pl from the one-copy
+// layout into v, decoded (shifted storage) as decode_pop does.
+template <int LAT, bool MASK, typename ST, typename SM, typename V>
+__device__ __forceinline__ void load_from_wide(const BoxT<ST> &b, int r, int c, int pl, const SM &sm, V &v)
+{
+    using B = BoxT<ST>;
+    const ST *q = b.wide() + r * B::WX + c - 2 + B::W;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) v[i] = decode_pop<LAT, MASK>(q[i * 12 * B::WX], i, r, c, pl, sm);
+}
+
 // The 27 populations of halo node (r, c) of ring plane pl from the box into
 // v, decoded (shifted storage) as decode_pop does.
 template <int LAT, bool MASK, typename ST, typename SM, typename V>
@@ -535,7 +554,8 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
                                         const uint8_t *__restrict__ mask,
                                         const ST *__restrict__ f, SM &sm, const TileF &T,
                                         int pl, int tid, const float *__restrict__ rho_src,
-                                        unsigned tbase = 0, const BoxT<ST> *box = nullptr)
+                                        unsigned tbase = 0, const BoxT<ST> *box = nullptr,
+                                        bool wide_box = false)
 {
     constexpr bool SHIFT = IsShifted<ST>::value;
     using L = LatF<LAT>;
@@ -578,7 +598,10 @@ __device__ __forceinline__ void phase_a(const GeoF &g, const PhysF &p,
             bool in_box = false;
             if constexpr (BOXED) in_box = sm.xok[c] && sm.yok[r];
             if (in_box) {
-                if constexpr (BOXED) load_from_box<LAT, MASK>(*box, r, c, pl, sm, fi[u]);
+                if constexpr (BOXED) {
+                    if (wide_box) load_from_wide<LAT, MASK>(*box, r, c, pl, sm, fi[u]);
+                    else          load_from_box<LAT, MASK>(*box, r, c, pl, sm, fi[u]);
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) fi[u][i] = decode_pop<LAT, MASK>(__ldg(f + (i * N + nk[u])), i, r, c, pl, sm);
@@ -1131,10 +1154,11 @@ k_step_f32_wstm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const float *
 constexpr int kBoxWarp = 7;
 constexpr int kBoxStages = 3, kBoxAhead = kBoxStages - 1;
 
-// The four box shapes as tensor maps of one population buffer: 32 x 8,
-// 32 x 2, W x 8 and W x 2 (x by y), one plane, all 27 populations.
+// The box shapes as tensor maps of one population buffer: 32 x 8, 32 x 2,
+// W x 8, W x 2 and the one-copy WX x 12 (x by y), one plane, all 27
+// populations.
 struct BoxMaps {
-    CUtensorMap mc, tc, ml, tl;
+    CUtensorMap mc, tc, ml, tl, wide;   // wide: the one-copy box, WX x 12
 };
 
 // Shared memory of the TMA-staged tile: that of the warp-specialised tile
@@ -1458,6 +1482,124 @@ k_step_shifted_wstm(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const ST 
     const unsigned tbase = sm.tmem;
     fused_tile_ws<LAT, MASK, true, ST, SharedSWS<LAT>>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y,
                                                        blockIdx.z, sm, tbase, rho_src, rho_dst);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tbase, COLS);
+}
+
+// ---- Tensor Memory form with TMA-staged planes, one thread group ---------
+// The Tensor Memory form of the shifted step (one group of 256 threads, a
+// block barrier per plane, two blocks per SM) with each entering plane's
+// 16-bit values copied into shared memory in one stage: the copy of plane
+// pl + 1 is requested once the block barrier after phase A of pl shows every
+// thread past the stage, and lands during phase B of pl. Tiles whose halo
+// stays inside the lattice take one copy per plane (BoxT::wide), the others
+// the nine boxes; one thread of warp 7 (whose phase A holds no halo node
+// beyond its interior one) issues them. A wait that runs out sets bit 2 of
+// the status and the block carries on with what shared memory holds (no
+// thread leaves the loop, so no block barrier is left waiting): the step
+// then reports LBM_ETIMEOUT.
+template <int LAT, typename ST> struct SharedSB : SharedS<LAT> {
+    alignas(128) BoxT<ST> box;
+    unsigned long long bfull;
+    unsigned char xok[SharedF<LAT>::AX], yok[SharedF<LAT>::AY];
+};
+
+template <int LAT, bool MASK, typename ST>
+__device__ __forceinline__ void fused_tile_tmb(const GeoF &g, const PhysF &p, const uint8_t *__restrict__ mask,
+                                               const ST *__restrict__ f, ST *__restrict__ fout,
+                                               int *__restrict__ status, int bx, int by, int bz,
+                                               SharedSB<LAT, ST> &sm, unsigned tbase, const BoxMaps *maps,
+                                               const float *__restrict__ rho_src, float *__restrict__ rho_dst)
+{
+    constexpr int TX = LatF<LAT>::TX, NT = TX * LatF<LAT>::TY;
+    constexpr int AX = SharedF<LAT>::AX, AY = SharedF<LAT>::AY;
+    constexpr int W = BoxT<ST>::W;
+    static_assert(LAT == 1 && TX == 32 && LatF<LAT>::TY == 8, "the box layout is that of D3Q27 32 x 8 tiles");
+    constexpr int kIssuer = 7 * 32;   // lane 0 of warp 7
+    const int tid = threadIdx.x;
+    const TileF T = tile_setup<LAT, ST>(g, bx, by, bz, sm, tid, NT, rho_src);
+    const bool inside = T.x0 + tid % TX < g.nx && T.y0 + tid / TX < g.ny;
+    const int xl = ((T.x0 - W) % g.nx + g.nx) % g.nx, xr = (T.x0 + 32) % g.nx;
+    const int yt = ((T.y0 - 2) % g.ny + g.ny) % g.ny, yb = (T.y0 + 8) % g.ny;
+    const bool wide = T.x0 - W >= 0 && T.x0 + 32 + W <= g.nx && T.y0 - 2 >= 0 && T.y0 + 10 <= g.ny;
+    if (tid < AX) {
+        const int c = tid;
+        const int xs = c < 2 ? xl + c + W - 2 : c < 34 ? T.x0 + c - 2 : xr + c - 34;
+        sm.xok[c] = xs < g.nx && xs == ((T.x0 - 2 + c) % g.nx + g.nx) % g.nx;
+    } else if (tid < AX + AY) {
+        const int r = tid - AX;
+        const int ys = r < 2 ? yt + r : r < 10 ? T.y0 + r - 2 : yb + r - 10;
+        sm.yok[r] = ys < g.ny && ys == ((T.y0 - 2 + r) % g.ny + g.ny) % g.ny;
+    }
+    if (tid == kIssuer) {
+        mbar_init(&sm.bfull, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (smem_u32(&sm.box) % 128u) {   // the boxes' 128-byte alignment rests on the base's
+        if (tid == 0) atomicOr(status, 8);
+        return;
+    }
+    // the copies of ring index r (plane z0 - 2 + r) into the stage
+    auto request = [&](int r) {
+        BoxT<ST> &b = sm.box;
+        unsigned long long *bar = &sm.bfull;
+        const int z = wrapf(T.z0 - 2 + r, g.nz);
+        if (wide) {
+            mbar_expect_tx(bar, BoxT<ST>::WIDE_BYTES);
+            tma_load_4d(&b.mc[0][0][0], &maps->wide, bar, T.x0 - W, T.y0 - 2, z);
+            return;
+        }
+        mbar_expect_tx(bar, BoxT<ST>::BYTES);
+        tma_load_4d(&b.mc[0][0][0], &maps->mc, bar, T.x0, T.y0, z);
+        tma_load_4d(&b.tc[0][0][0], &maps->tc, bar, T.x0, yt, z);
+        tma_load_4d(&b.bc[0][0][0], &maps->tc, bar, T.x0, yb, z);
+        tma_load_4d(&b.ml[0][0][0], &maps->ml, bar, xl, T.y0, z);
+        tma_load_4d(&b.mr[0][0][0], &maps->ml, bar, xr, T.y0, z);
+        tma_load_4d(&b.tl[0][0][0], &maps->tl, bar, xl, yt, z);
+        tma_load_4d(&b.tr[0][0][0], &maps->tl, bar, xr, yt, z);
+        tma_load_4d(&b.bl[0][0][0], &maps->tl, bar, xl, yb, z);
+        tma_load_4d(&b.br[0][0][0], &maps->tl, bar, xr, yb, z);
+    };
+    if (tid == kIssuer) request(0);
+    bool copies = true;   // no wait has run out (after one has, the copies stop)
+    for (int pl = 0; pl < T.np; ++pl) {
+        if (copies && !mbar_wait(&sm.bfull, pl & 1)) {
+            atomicOr(status, 2);
+            copies = false;
+        }
+        phase_a<LAT, MASK, true, false, false, true>(g, p, mask, f, sm, T, pl, tid, rho_src, tbase, &sm.box,
+                                                     wide);
+        __syncthreads();
+        if (tid == kIssuer && copies && pl + 1 < T.np) {   // every thread is past the stage
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            request(pl + 1);
+        }
+        if (pl >= 4) phase_b<LAT, MASK, true>(g, p, mask, f, fout, status, sm, T, pl, tid, rho_dst, tbase, inside);
+    }
+}
+
+// Shifted 16-bit storage: Tensor Memory form with TMA-staged planes (D3Q27
+// 32 x 8 tiles, nx a multiple of 8), TmemF::COLS columns of Tensor Memory and
+// sizeof(SharedSB<LAT, ST>) bytes of dynamic shared memory per block.
+template <int LAT, typename ST, bool MASK>
+__global__ void __launch_bounds__(LatF<LAT>::TX * LatF<LAT>::TY, 2)
+k_step_shifted_tmtma(GeoF g, PhysF p, const uint8_t *__restrict__ mask, const __grid_constant__ BoxMaps maps,
+                     const ST *__restrict__ f, ST *__restrict__ fout, const float *__restrict__ rho_src,
+                     float *__restrict__ rho_dst, int *__restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw128[];
+    SharedSB<LAT, ST> &sm = *reinterpret_cast<SharedSB<LAT, ST> *>(smem_raw128);
+    constexpr unsigned COLS = TmemF<LAT>::COLS;
+    if (threadIdx.x < 32) tmem_alloc(&sm.tmem, COLS);
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const unsigned tbase = sm.tmem;
+    fused_tile_tmb<LAT, MASK, ST>(g, p, mask, f, fout, status, blockIdx.x, blockIdx.y, blockIdx.z, sm, tbase,
+                                  &maps, rho_src, rho_dst);
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();

@@ -26,4 +26,12 @@ void launch_shifted(const lbmf::GeoF &g, const lbmf::PhysF &p, const uint8_t *ma
                     const ST *src, ST *dst, const float *rho_src, float *rho_dst, int *status, bool solid,
                     cudaStream_t s);
 
+// The one-thread-group Tensor Memory form of the shifted step with TMA-staged
+// planes (k_step_shifted_tmtma): the same arguments; 256 threads and
+// sizeof(SharedSB<1, ST>) bytes of shared memory per block, two per SM.
+template <typename ST>
+void launch_shifted_tm(const lbmf::GeoF &g, const lbmf::PhysF &p, const uint8_t *mask, const lbmf::BoxMaps &maps,
+                       const ST *src, ST *dst, const float *rho_src, float *rho_dst, int *status, bool solid,
+                       cudaStream_t s);
+
 }  // namespace lbmtma

@@ -18,10 +18,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 D2Q9, D3Q27 = 0, 1
 EOS_VDW, EOS_PR, EOS_RKS, EOS_CS, EOS_SC1, EOS_SC2 = 0, 1, 2, 3, 4, 5
 F64, F32, F16S, BF16S = 0, 1, 2, 3
-FUSED_PLAIN, FUSED_WARP_SPECIALISED, FUSED_TMEM, FUSED_WS_TMEM, FUSED_WS_TMA = 0, 1, 2, 3, 4
+FUSED_PLAIN, FUSED_WARP_SPECIALISED, FUSED_TMEM, FUSED_WS_TMEM, FUSED_WS_TMA, FUSED_TM_TMA = 0, 1, 2, 3, 4, 5
 FUSED_NAMES = {0: "plain", 1: "warp-specialised", 2: "tensor-memory",
                3: "warp-specialised, tensor-memory",
-               4: "warp-specialised, tensor-memory, TMA-staged planes"}
+               4: "warp-specialised, tensor-memory, TMA-staged planes",
+               5: "tensor-memory, TMA-staged planes (shifted storage)"}
 FLAG_PHI_OFF = 1
 FLAG_EOS_F64 = 2
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
@@ -327,7 +328,8 @@ class LBM:
 
     def set_fused_variant(self, variant: int):
         """Form of the fused step: FUSED_PLAIN, FUSED_WARP_SPECIALISED,
-        FUSED_TMEM, FUSED_WS_TMEM or FUSED_WS_TMA (bitwise the same results)."""
+        FUSED_TMEM, FUSED_WS_TMEM, FUSED_WS_TMA or (shifted storage)
+        FUSED_TM_TMA (bitwise the same results)."""
         self._check(_lib.lbm_set_fused_variant(self._h, int(variant)))
 
     @property

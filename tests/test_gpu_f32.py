@@ -232,6 +232,8 @@ def test_f32_tma_staged_form_rejects_other_cases(lbm):
         with pytest.raises(lbm.LBMError):
             g.set_fused_variant(lbm.FUSED_WS_TMA)
     g = lbm.LBM(1, 64, 16, 12, w.eos, w.t_over_tc, w.kappa, w.tau, a=w.a, b=w.b, storage=lbm.F32)
+    with pytest.raises(lbm.LBMError):   # the one-group TMA-staged form is one of shifted storage
+        g.set_fused_variant(lbm.FUSED_TM_TMA)
     g.set_tile(7)
     with pytest.raises(lbm.LBMError):
         g.set_fused_variant(lbm.FUSED_WS_TMA)

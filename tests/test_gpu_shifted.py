@@ -147,10 +147,10 @@ def test_shifted_tensor_memory_form_is_bitwise_the_plain_one(lbm, storage, latti
 @pytest.mark.parametrize("shape,chunk,solid", [((64, 37, 30), 7, False), ((96, 40, 24), 24, True),
                                               ((40, 24, 20), 1, True)])
 def test_shifted_tma_staged_form_is_bitwise_the_plain_one(lbm, storage, shape, chunk, solid):
-    """The TMA-staged form of the shifted step (each entering plane's 16-bit
-    values on the halo copied into shared memory by nine bulk tensor copies,
-    decoded by the producers with their source-density ring) against the
-    plain form: interior and edge tiles, a ragged y extent, chunks of one
+    """The TMA-staged forms of the shifted step (each entering plane's 16-bit
+    values on the halo copied into shared memory, one copy or nine per plane,
+    decoded with the source-density ring; warp-specialised, and one thread
+    group with a single stage) against the plain form: interior and edge tiles, a ragged y extent, chunks of one
     plane, solid nodes; bitwise the same after 20 steps (graph replays and
     a plain launch)."""
     w = inputs.DROP_D3Q27_128
@@ -158,7 +158,7 @@ def test_shifted_tma_staged_form_is_bitwise_the_plain_one(lbm, storage, shape, c
     mask = inputs.pillar_mask(nx, ny, nz, 2, 4, 6) if solid else None
     rho = inputs.add_noise(inputs.drop(nx, ny, nz, min(nx, ny, nz) / 4.0, w.rho_v, w.rho_l), 1e-4, 19)
     out = []
-    for variant in (0, 4):
+    for variant in (0, 4, 5):
         g = lbm.LBM(1, nx, ny, nz, w.eos, w.t_over_tc, w.kappa, 0.8, a=w.a, b=w.b, mask=mask,
                     rho_w=w.rho_v, storage=storage)
         g.set_fused_variant(variant)
@@ -169,7 +169,7 @@ def test_shifted_tma_staged_form_is_bitwise_the_plain_one(lbm, storage, shape, c
         assert g.fused_variant == variant
         out.append(g.get_populations())
     assert np.all(np.isfinite(out[0]))
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("storage", [2, 3])
